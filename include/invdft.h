@@ -1,0 +1,206 @@
+/*
+ * invdft.h -- C ABI of the B300 inverse-DFT hot-path library (libinvdft.so).
+ *
+ * The library implements, on one GPU, the data-parallel hot path of the
+ * adjoint-based inverse density-functional method of arXiv 2510.10529
+ * ("invDFT"):
+ *   - the finite-element Kohn-Sham Hamiltonian in standard form,
+ *     H~ = M^-1/2 H M^-1/2 = D K D + diag(v)   (Eq. 17, Eq. 19),
+ *     applied cell by cell to blocks of vectors (Sec. 3.2.3);
+ *   - the Chebyshev-filtered subspace iteration with Rayleigh-Ritz
+ *     (Sec. 3.2.2, Eq. 23-24) for the lowest eigenpairs;
+ *   - Fermi-Dirac occupations and the density (Eq. 4, Eq. 5);
+ *   - the loss (Eq. 1), the projected adjoint solves by preconditioned MINRES
+ *     (Eq. 7-10, Eq. 20, Sec. 3.2.2) and the gradient dL/dv_xc (Eq. 11, 22)
+ *     with the far-field mask (Sec. 3.1.2);
+ *   - the limited-memory BFGS update of v_xc (Eq. 21).
+ *
+ * Discretisation (shared by every entry point): a uniform box [lo,hi]^3 cut
+ * into ncell^3 cubic cells of order p (2 or 4) with nodes at the
+ * Gauss-Lobatto-Legendre points (spectral elements, Sec. 3.2.1).  Boundary
+ * nodes carry psi = p = 0; the L = (ncell*p - 1)^3 interior nodes are the
+ * unknowns, numbered lexicographically with x fastest, then y, then z.
+ *
+ * Data layout: every nodal multivector is node-major ("row-major" in the
+ * paper's words, Sec. 3.2.3): element (a, j) of an [L][ncol] block is at
+ * a*ncol + j.  Nodal scalar fields are [L].  All arrays are C-contiguous.
+ *
+ * Ownership: the caller owns every array it passes.  Arrays documented as
+ * "device" must be device pointers of the current CUDA device; "host" arrays
+ * are host pointers.  The handle keeps pointers to nothing the caller owns
+ * except the workspace bound by invdft_bind_workspace, which must stay valid
+ * (and unused by anyone else) until the handle is destroyed or rebound.
+ *
+ * Streams: every call is enqueued on `stream` (a cudaStream_t passed as
+ * void*; NULL is the legacy default stream).  Calls that return host values
+ * (loss, stats, iteration counts) synchronise that stream before returning.
+ *
+ * Errors: every call returns an invdft_status and never throws across the
+ * ABI.  On failure the text of the last error is available from
+ * invdft_last_error(handle) (or invdft_last_error(NULL) for failures before a
+ * handle exists).  INVDFT_ENOCONV leaves valid, flagged results.
+ *
+ * Threading: a handle is not thread safe; distinct handles are independent.
+ */
+#ifndef INVDFT_H
+#define INVDFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct invdft_ctx *invdft_handle;
+
+typedef enum {
+  INVDFT_OK = 0,
+  INVDFT_EINVAL = 1,    /* bad argument, shape, order or state            */
+  INVDFT_ENOMEM = 2,    /* workspace missing or too small                 */
+  INVDFT_ECUDA = 3,     /* a CUDA runtime error; text in last_error       */
+  INVDFT_ENOCONV = 4,   /* an iteration cap was reached; results flagged  */
+  INVDFT_ETIMEOUT = 5,  /* a bounded device wait expired                  */
+  INVDFT_ENOTSPD = 6    /* Cholesky of the subspace overlap failed        */
+} invdft_status;
+
+typedef enum {
+  INVDFT_FP64 = 0,      /* every step in FP64                                     */
+  INVDFT_MIXED = 1      /* FP32 storage, TF32 tensor-core cell products with FP32
+                           accumulation in the Chebyshev filter and the inner
+                           MINRES iterations; FP64 for Rayleigh-Ritz, Cholesky,
+                           residuals, refinement and every reduction             */
+} invdft_precision;
+
+/* Mesh: box [lo,hi]^3, ncell cells per axis, element order (2 or 4). */
+typedef struct {
+  double lo, hi;
+  int ncell;
+  int order;
+} invdft_mesh_desc;
+
+/* Solver options.  Zero fields take the defaults given in brackets.
+ * c_eig, c_ad, tau_bc default to the paper's values (Sec. 4.2.4). */
+typedef struct {
+  int nstates;            /* N_v in [1, 96]: Ritz vectors (occupied + buffer)  */
+  double n_electrons;     /* N_e (Eq. 5)                                        */
+  double kT;              /* k_B T in Ha; 0 = closed shell (N_e even)           */
+  int cheb_degree;        /* Chebyshev filter degree m                  [20]   */
+  double c_eig;           /* t_eig = e_L2^2 / c_eig                     [1e2]  */
+  double c_ad;            /* t_ad  = e_L2^2 / c_ad                      [1e5]  */
+  double tau_bc;          /* gradient mask threshold on rho_data        [1e-6] */
+  double eig_tol;         /* fixed eigen-residual tolerance if > 0; else the
+                             adaptive rule with floor 1e-10                     */
+  double adj_tol;         /* fixed relative adjoint tolerance if > 0; else the
+                             adaptive rule with floor 1e-10                     */
+  int max_cheb_passes;    /* cap on filter + Rayleigh-Ritz passes       [60]   */
+  int max_minres_iters;   /* cap on inner MINRES iterations per solve   [2000] */
+  int lbfgs_history;      /* L-BFGS pairs kept                          [10]   */
+  invdft_precision prec;  /* FP64 or MIXED                                      */
+  unsigned long long seed;/* seed of the random start block                     */
+  double deg_tol;         /* eigenvalues closer than this form a degenerate
+                             set (Ha)                                   [1e-8] */
+} invdft_opts;
+
+/* Per-call statistics (host struct filled by the calls that take it). */
+typedef struct {
+  double loss, err_l2, n_elec, mu;
+  double eig_resid_max;   /* max standard-form residual over occupied states   */
+  double adj_resid_max;   /* max relative true residual of the adjoint solves  */
+  double eta;             /* multiplier of Eq. 9                               */
+  int cheb_passes, hx_calls, minres_iters_max, ls_trials, refinements;
+  double t_forward_ms, t_adjoint_ms;
+} invdft_stats;
+
+/* Create a handle for one problem.  Computes the GLL rule, the element
+ * matrices and the lumped mass on the host; allocates nothing on the device.
+ * n_nodes_out (optional) receives L.                                        */
+invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts *opts,
+                                 invdft_handle *out, long long *n_nodes_out);
+invdft_status invdft_destroy(invdft_handle h);
+
+/* Device scratch needed by the solvers for this mesh and these options.
+ * The caller allocates it (e.g. as a torch uint8 tensor) and binds it; the
+ * handle then uploads its tables and keeps orbitals, the L-BFGS history and
+ * every work vector there.  apply_h with ncol <= nstates needs the same
+ * workspace.  Binding again moves the handle to the new region (state is
+ * reset).                                                                   */
+invdft_status invdft_workspace_size(invdft_handle h, size_t *bytes);
+invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t bytes,
+                                    void *stream);
+
+/* Host output: xyz [L][3] coordinates (bohr) of the unknown nodes.          */
+invdft_status invdft_node_coords(invdft_handle h, double *xyz_host);
+/* Device output: m [L], the lumped (GLL) mass diagonal = quadrature weights.*/
+invdft_status invdft_mass_diag(invdft_handle h, double *m_dev, void *stream);
+
+/* Set the potential: v = v_fixed + v_xc at the unknown nodes (device [L]).
+ * v_fixed = v_ext + v_H[rho_data] (Eq. 2); v_xc may be NULL (zero).        */
+invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed_dev,
+                                   const double *v_xc_dev, void *stream);
+
+/* Y = H~ X for an [L][ncol] block (Eq. 19, Sec. 3.2.3), device pointers.
+ * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED: X, Y are float.
+ * ncol in [1, 256].  The operator used is the one of the last
+ * invdft_set_potential.                                                     */
+invdft_status invdft_apply_h(invdft_handle h, const void *X_dev, void *Y_dev, int ncol,
+                             invdft_precision prec, void *stream);
+
+/* Chebyshev filter Y = p_m(H~) X with p_m(t) = T_m((t-c)/e)/T_m((a0-c)/e),
+ * e = (b-a)/2, c = (b+a)/2, by the scaled three-term recurrence (Sec. 3.2.2).
+ * X, Y: device [L][ncol] in the precision `prec` (double or float).  Exposed
+ * for testing the filter on its own.                                        */
+invdft_status invdft_chebyshev_filter(invdft_handle h, const void *X_dev, void *Y_dev,
+                                      int ncol, int degree, double a, double b, double a0,
+                                      invdft_precision prec, void *stream);
+
+/* Forward Kohn-Sham solve at the current potential (Sec. 3.2.2):
+ * Chebyshev-filtered subspace iteration with FP64 Rayleigh-Ritz until the
+ * largest residual over occupied states is below the eigen tolerance.
+ * psi: device [L][nstates] standard-form orbitals psi~ (out; also the warm
+ * start kept inside the handle); eps, occ: device [nstates]; rho: device [L].
+ * Any output pointer may be NULL.                                           */
+invdft_status invdft_forward_solve(invdft_handle h, double *psi_dev, double *eps_dev,
+                                   double *occ_dev, double *rho_dev, invdft_stats *stats,
+                                   void *stream);
+
+/* Adjoint solve for a generic upstream dL/drho (device [L]) around the last
+ * forward solve: returns p~ (device [L][nstates], zero for empty states)
+ * (Eq. 7-10, 20).  The paper's loss has dL/drho_a = -2 m_a w_a (rho_d-rho)_a.
+ * The relative tolerance is opts.adj_tol if set, else the adaptive rule.    */
+invdft_status invdft_adjoint_solve(invdft_handle h, const double *dL_drho_dev, double *p_dev,
+                                   invdft_stats *stats, void *stream);
+
+/* Vector-Jacobian product of the density map v -> rho(v) around the last
+ * forward solve: grad_v = sum_i p~_i o psi~_i with p~ the adjoint functions
+ * for the upstream dL/drho (device [L] in, device [L] out, no far-field
+ * mask).  This is the backward of the Kohn-Sham solve (Eq. 7-11).          */
+invdft_status invdft_density_vjp(invdft_handle h, const double *dL_drho_dev, double *grad_v_dev,
+                                 invdft_stats *stats, void *stream);
+
+/* Loss and masked gradient at the current potential: forward solve, loss
+ * (Eq. 1), adjoint and grad_b = sum_i p~_bi psi~_bi, zero where
+ * rho_data < tau_bc (Eq. 11, 22, Sec. 3.1.2).  rho_data, w, grad: device [L];
+ * loss_out: host scalar (optional).                                          */
+invdft_status invdft_loss_grad(invdft_handle h, const double *rho_data_dev, const double *w_dev,
+                               double *loss_out, double *grad_dev, invdft_stats *stats,
+                               void *stream);
+
+/* One inverse iteration (Eq. 21): L-BFGS direction from the history kept in
+ * the handle, backtracking line search (one forward solve per trial), then
+ * loss, adjoint and gradient at the accepted point.  v_xc: device [L], in/out.
+ * The potential of the handle becomes v_fixed + v_xc(new).  The first call
+ * after set_potential/reset evaluates the gradient at the incoming v_xc.     */
+invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const double *w_dev,
+                          double *v_xc_dev, invdft_stats *stats, void *stream);
+
+/* Forget the L-BFGS history and the warm-start orbitals.                   */
+invdft_status invdft_reset(invdft_handle h);
+
+/* Text of the last error on this handle (or of the last create failure if
+ * h is NULL).  Valid until the next call on the handle.                     */
+const char *invdft_last_error(invdft_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INVDFT_H */

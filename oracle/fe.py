@@ -224,3 +224,41 @@ class Mesh:
     def assemble_Htilde(self, v: np.ndarray) -> sp.csr_matrix:
         d = sp.diags(1.0 / np.sqrt(self.mass()))
         return (d @ self.assemble_K() @ d + sp.diags(v)).tocsr()
+
+
+def htilde_rows(mesh: Mesh, v_rows: np.ndarray, rows: np.ndarray, fetch_X) -> np.ndarray:
+    """(H~ X)[rows] one row at a time from the definition (Eq. 17, Eq. 19).
+
+    For interior node a = rows[k]: (D K D X)_a = d_a sum over the cells e that
+    contain a of sum_b K_e[a_loc, b_loc] d_b X_b, plus v_a X_a.
+    fetch_X(idx) must return X at the interior indices idx ([len(idx), ncol]),
+    so that only the neighbourhoods of the sampled rows are needed.
+    """
+    p, q, Ni = mesh.p, mesh.q, mesh.Ni
+    m1 = mesh.m1
+    out = []
+    for k, a in enumerate(rows):
+        ix, iy, iz = a % Ni + 1, (a // Ni) % Ni + 1, a // (Ni * Ni) + 1   # full-grid
+        acc = None
+        for cz in {(iz - 1) // p, iz // p} & set(range(mesh.n)):
+            for cy in {(iy - 1) // p, iy // p} & set(range(mesh.n)):
+                for cx in {(ix - 1) // p, ix // p} & set(range(mesh.n)):
+                    lx, ly, lz = ix - cx * p, iy - cy * p, iz - cz * p
+                    if not (0 <= lx <= p and 0 <= ly <= p and 0 <= lz <= p):
+                        continue
+                    aloc = lx + q * ly + q * q * lz
+                    idx, dvals, bloc = [], [], []
+                    for bz in range(q):
+                        for by in range(q):
+                            for bx in range(q):
+                                gx, gy, gz = cx * p + bx, cy * p + by, cz * p + bz
+                                if 1 <= gx <= Ni and 1 <= gy <= Ni and 1 <= gz <= Ni:
+                                    idx.append((gx - 1) + Ni * ((gy - 1) + Ni * (gz - 1)))
+                                    dvals.append((m1[gx] * m1[gy] * m1[gz]) ** -0.5)
+                                    bloc.append(bx + q * by + q * q * bz)
+                    Xb = fetch_X(np.array(idx))
+                    contrib = (mesh.Ke[aloc, bloc] * np.array(dvals)) @ Xb
+                    acc = contrib if acc is None else acc + contrib
+        da = (m1[ix] * m1[iy] * m1[iz]) ** -0.5
+        out.append(da * acc + v_rows[k] * fetch_X(np.array([a]))[0])
+    return np.array(out)

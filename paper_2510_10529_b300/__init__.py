@@ -1,0 +1,270 @@
+"""B300 inverse-DFT hot path (arXiv 2510.10529) -- Python binding of libinvdft.
+
+Thin layer over the C ABI of include/invdft.h.  Functions named `invdft_*`
+forward to the entry point of the same name; torch CUDA tensors supply device
+memory and the current CUDA stream.  `Problem` owns one handle and its
+workspace tensor; `KohnShamDensity` is a torch.autograd.Function whose forward
+is the Kohn-Sham solve and whose backward is the adjoint solve plus the
+gradient reduction (Eq. 7-11), both run by the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_MIXED, INVDFT_OK, InvdftError, MeshDesc,
+                   Opts, Stats, check, lib)
+
+__all__ = ["Problem", "KohnShamDensity", "MeshDesc", "Opts", "Stats", "InvdftError",
+           "INVDFT_FP64", "INVDFT_MIXED", "library_path"]
+
+
+def library_path() -> str:
+    from ._lib import LIB_PATH
+    return LIB_PATH
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ok(name, st, h, allow_noconv=True):
+    if st == INVDFT_OK or (allow_noconv and st == INVDFT_ENOCONV):
+        return st
+    return check(name, st, h)
+
+
+# ----------------------------------------------------------- same-name wrappers
+
+def invdft_create_mesh(mesh: MeshDesc, opts: Opts):
+    h = C.c_void_p()
+    n = C.c_longlong()
+    _ok("invdft_create_mesh", lib.invdft_create_mesh(C.byref(mesh), C.byref(opts), C.byref(h),
+                                                     C.byref(n)), None, False)
+    return h, n.value
+
+
+def invdft_destroy(h):
+    return lib.invdft_destroy(h)
+
+
+def invdft_workspace_size(h) -> int:
+    n = C.c_size_t()
+    _ok("invdft_workspace_size", lib.invdft_workspace_size(h, C.byref(n)), h, False)
+    return n.value
+
+
+def invdft_bind_workspace(h, ws: torch.Tensor):
+    return _ok("invdft_bind_workspace",
+               lib.invdft_bind_workspace(h, _ptr(ws), ws.numel() * ws.element_size(), _stream()),
+               h, False)
+
+
+def invdft_node_coords(h, L: int) -> np.ndarray:
+    xyz = np.empty((L, 3), dtype=np.float64)
+    _ok("invdft_node_coords", lib.invdft_node_coords(h, xyz.ctypes.data_as(C.c_void_p)), h, False)
+    return xyz
+
+
+def invdft_mass_diag(h, m: torch.Tensor):
+    return _ok("invdft_mass_diag", lib.invdft_mass_diag(h, _ptr(m), _stream()), h, False)
+
+
+def invdft_set_potential(h, v_fixed: torch.Tensor, v_xc: torch.Tensor | None):
+    return _ok("invdft_set_potential",
+               lib.invdft_set_potential(h, _ptr(v_fixed), _ptr(v_xc), _stream()), h, False)
+
+
+def invdft_apply_h(h, X: torch.Tensor, Y: torch.Tensor):
+    prec = INVDFT_FP64 if X.dtype == torch.float64 else INVDFT_MIXED
+    if X.dtype != Y.dtype or X.dtype not in (torch.float64, torch.float32):
+        raise ValueError("apply_h: X and Y must both be float64 or both float32")
+    ncol = X.shape[1] if X.dim() == 2 else 1
+    return _ok("invdft_apply_h", lib.invdft_apply_h(h, _ptr(X), _ptr(Y), ncol, prec, _stream()),
+               h, False)
+
+
+def invdft_chebyshev_filter(h, X, Y, degree, a, b, a0):
+    prec = INVDFT_FP64 if X.dtype == torch.float64 else INVDFT_MIXED
+    return _ok("invdft_chebyshev_filter",
+               lib.invdft_chebyshev_filter(h, _ptr(X), _ptr(Y), X.shape[1], degree, a, b, a0,
+                                           prec, _stream()), h, False)
+
+
+def invdft_forward_solve(h, psi=None, eps=None, occ=None, rho=None):
+    st = Stats()
+    code = _ok("invdft_forward_solve", lib.invdft_forward_solve(
+        h, _ptr(psi), _ptr(eps), _ptr(occ), _ptr(rho), C.byref(st), _stream()), h)
+    return code, st
+
+
+def invdft_adjoint_solve(h, dL_drho, p):
+    st = Stats()
+    code = _ok("invdft_adjoint_solve",
+               lib.invdft_adjoint_solve(h, _ptr(dL_drho), _ptr(p), C.byref(st), _stream()), h)
+    return code, st
+
+
+def invdft_density_vjp(h, dL_drho, grad_v):
+    st = Stats()
+    code = _ok("invdft_density_vjp",
+               lib.invdft_density_vjp(h, _ptr(dL_drho), _ptr(grad_v), C.byref(st), _stream()), h)
+    return code, st
+
+
+def invdft_loss_grad(h, rho_data, w, grad):
+    st = Stats()
+    loss = C.c_double()
+    code = _ok("invdft_loss_grad", lib.invdft_loss_grad(
+        h, _ptr(rho_data), _ptr(w), C.byref(loss), _ptr(grad), C.byref(st), _stream()), h)
+    return code, loss.value, st
+
+
+def invdft_step(h, rho_data, w, v_xc):
+    st = Stats()
+    code = _ok("invdft_step", lib.invdft_step(h, _ptr(rho_data), _ptr(w), _ptr(v_xc),
+                                              C.byref(st), _stream()), h)
+    return code, st
+
+
+def invdft_reset(h):
+    return lib.invdft_reset(h)
+
+
+# ----------------------------------------------------------- owning wrapper
+
+class Problem:
+    """One inverse-DFT problem: a handle plus its torch-allocated workspace."""
+
+    def __init__(self, lo, hi, ncell, order, nstates, n_electrons=0.0, kT=0.0,
+                 prec="fp64", cheb_degree=0, eig_tol=0.0, adj_tol=0.0, tau_bc=0.0,
+                 max_cheb_passes=0, max_minres_iters=0, lbfgs_history=0, seed=1,
+                 deg_tol=0.0, device=None):
+        self.device = torch.device(device or "cuda")
+        mesh = MeshDesc(lo=float(lo), hi=float(hi), ncell=int(ncell), order=int(order))
+        opts = Opts(nstates=int(nstates), n_electrons=float(n_electrons), kT=float(kT),
+                    cheb_degree=int(cheb_degree), c_eig=0.0, c_ad=0.0, tau_bc=float(tau_bc),
+                    eig_tol=float(eig_tol), adj_tol=float(adj_tol),
+                    max_cheb_passes=int(max_cheb_passes), max_minres_iters=int(max_minres_iters),
+                    lbfgs_history=int(lbfgs_history),
+                    prec=INVDFT_MIXED if prec == "mixed" else INVDFT_FP64, seed=int(seed),
+                    deg_tol=float(deg_tol))
+        self.h, self.L = invdft_create_mesh(mesh, opts)
+        self.nstates = int(nstates)
+        nbytes = invdft_workspace_size(self.h)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            invdft_bind_workspace(self.h, self.workspace)
+        self.potential_version = 0
+        self.solved_version = -1
+
+    def close(self):
+        if self.h:
+            invdft_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self, *shape, dtype=torch.float64):
+        return torch.zeros(*shape, dtype=dtype, device=self.device)
+
+    def coords(self) -> np.ndarray:
+        return invdft_node_coords(self.h, self.L)
+
+    def mass(self) -> torch.Tensor:
+        m = self.zeros(self.L)
+        invdft_mass_diag(self.h, m)
+        return m
+
+    def set_potential(self, v_fixed, v_xc=None):
+        invdft_set_potential(self.h, v_fixed, v_xc)
+        self.v_fixed = v_fixed
+        self.potential_version += 1
+
+    def apply_h(self, X):
+        Y = torch.empty_like(X)
+        invdft_apply_h(self.h, X, Y)
+        return Y
+
+    def chebyshev_filter(self, X, degree, a, b, a0):
+        Y = torch.empty_like(X)
+        invdft_chebyshev_filter(self.h, X, Y, degree, a, b, a0)
+        return Y
+
+    def forward_solve(self):
+        psi = self.zeros(self.L, self.nstates)
+        eps = self.zeros(self.nstates)
+        occ = self.zeros(self.nstates)
+        rho = self.zeros(self.L)
+        code, st = invdft_forward_solve(self.h, psi, eps, occ, rho)
+        self.solved_version = self.potential_version
+        return dict(psi=psi, eps=eps, occ=occ, rho=rho, stats=st.as_dict(), code=code)
+
+    def adjoint_solve(self, dL_drho):
+        p = self.zeros(self.L, self.nstates)
+        code, st = invdft_adjoint_solve(self.h, dL_drho, p)
+        return p, st.as_dict()
+
+    def density_vjp(self, dL_drho):
+        g = self.zeros(self.L)
+        code, st = invdft_density_vjp(self.h, dL_drho, g)
+        return g, st.as_dict()
+
+    def loss_grad(self, rho_data, w):
+        g = self.zeros(self.L)
+        code, loss, st = invdft_loss_grad(self.h, rho_data, w, g)
+        self.solved_version = self.potential_version
+        return loss, g, st.as_dict()
+
+    def step(self, rho_data, w, v_xc):
+        code, st = invdft_step(self.h, rho_data, w, v_xc)
+        self.potential_version += 1
+        self.solved_version = self.potential_version
+        return st.as_dict()
+
+    def reset(self):
+        invdft_reset(self.h)
+
+
+class KohnShamDensity(torch.autograd.Function):
+    """rho(v_xc): forward = Kohn-Sham solve (Sec. 3.2.2), backward = adjoint
+    solve + gradient reduction for the incoming dL/drho (Eq. 7-11).
+
+    Orbitals are not stored by autograd: the handle keeps those of its last
+    solve, and backward re-solves at the saved v_xc when another solve has
+    happened in between.
+    """
+
+    @staticmethod
+    def forward(ctx, v_xc, problem: Problem, v_fixed):
+        problem.set_potential(v_fixed, v_xc.detach().contiguous())
+        out = problem.forward_solve()
+        ctx.problem = problem
+        ctx.version = problem.potential_version
+        ctx.save_for_backward(v_xc.detach(), v_fixed)
+        return out["rho"]
+
+    @staticmethod
+    def backward(ctx, grad_rho):
+        problem = ctx.problem
+        v_xc, v_fixed = ctx.saved_tensors
+        if problem.solved_version != ctx.version:
+            problem.set_potential(v_fixed, v_xc.contiguous())
+            problem.forward_solve()
+            ctx.version = problem.potential_version
+        g, _ = problem.density_vjp(grad_rho.contiguous().to(torch.float64))
+        return g, None, None

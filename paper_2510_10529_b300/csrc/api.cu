@@ -1,0 +1,321 @@
+// C-ABI entry points of libinvdft (declared in include/invdft.h): handle
+// life cycle, workspace binding, tables, potential, and the operator calls.
+// The solver entry points (forward, adjoint, loss/gradient, step) live in
+// solvers.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "solvers.h"
+
+using namespace invdft;
+
+namespace invdft {
+
+static thread_local std::string g_create_error;
+
+bool cuda_ok(Ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return true;
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  if (c) c->err = buf;
+  return false;
+}
+
+namespace {
+
+__global__ void init_fields(const double *__restrict__ m1, const double *__restrict__ kA,
+                            const double *__restrict__ kB, int Ni, double *__restrict__ mass,
+                            double *__restrict__ dvec, double *__restrict__ prec) {
+  const long long L = (long long)Ni * Ni * Ni;
+  for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < L;
+       a += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(a % Ni) + 1, iy = (int)((a / Ni) % Ni) + 1, iz = (int)(a / ((long long)Ni * Ni)) + 1;
+    const double m = m1[ix] * m1[iy] * m1[iz];
+    const double kaa = 0.5 * (kB[iz] * kB[iy] * kA[ix] + kB[iz] * kA[iy] * kB[ix] +
+                              kA[iz] * kB[iy] * kB[ix]);
+    mass[a] = m;
+    dvec[a] = 1.0 / sqrt(m);
+    prec[a] = m / kaa;          // inverse diagonal of D K D (Laplacian part)
+  }
+}
+
+__global__ void add_fields(const double *__restrict__ a, const double *__restrict__ b,
+                           double *__restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = a[i] + (b ? b[i] : 0.0);
+}
+
+int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
+
+// Lay out (or, with base == nullptr, only measure) the workspace.
+size_t plan(Ctx *c, char *base) {
+  Arena ar;
+  ar.base = base;
+  const long long L = c->L;
+  const int nv = c->nv;
+  const int N = c->g.Ni + 2;
+  const size_t blk = (size_t)L * nv;
+  c->dm1 = ar.take<double>(N);
+  c->m1tab = ar.take<double>(N);
+  c->kAtab = ar.take<double>(N);
+  c->kBtab = ar.take<double>(N);
+  c->mass = ar.take<double>(L);
+  c->dvec = ar.take<double>(L);
+  c->prec_diag = ar.take<double>(L);
+  c->v = ar.take<double>(L);
+  c->vfixed = ar.take<double>(L);
+  c->rho = ar.take<double>(L);
+  c->grad = ar.take<double>(L);
+  c->grad_new = ar.take<double>(L);
+  c->dir = ar.take<double>(L);
+  c->vtry = ar.take<double>(L);
+  c->dLdrho = ar.take<double>(L);
+  c->X = ar.take<double>(blk);
+  c->Y = ar.take<double>(blk);
+  c->HY = ar.take<double>(blk);
+  c->P = ar.take<double>(blk);
+  c->Rg = ar.take<double>(blk);
+  c->C0 = ar.take<double>(blk);
+  c->C1 = ar.take<double>(blk);
+  c->C2 = ar.take<double>(blk);
+  c->E32 = ar.take<float>(blk);
+  for (int k = 0; k < 9; ++k) c->mr[k] = ar.take<double>(blk);
+  const int hist = c->o.lbfgs_history;
+  c->Sh = ar.take<double>((size_t)hist * L);
+  c->Yh = ar.take<double>((size_t)hist * L);
+  c->eps = ar.take<double>(kMaxGram);
+  c->occ = ar.take<double>(kMaxGram);
+  c->dfde = ar.take<double>(kMaxGram);
+  c->small = ar.take<double>(16 * (size_t)kMaxGram * kMaxGram);
+  c->partial = ar.take<double>((size_t)kGramBlocks * kMaxGram * kMaxGram);
+  c->scal = ar.take<double>(1024 * (size_t)kMaxCols);
+  c->status = ar.take<int>(16);
+  return ar.off + 256;
+}
+
+}  // namespace
+}  // namespace invdft
+
+extern "C" {
+
+invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts *opts,
+                                 invdft_handle *out, long long *n_nodes_out) {
+  if (!mesh || !opts || !out) {
+    g_create_error = "create_mesh: null argument";
+    return INVDFT_EINVAL;
+  }
+  *out = nullptr;
+  if (!(mesh->order == 2 || mesh->order == 4) || mesh->ncell < 1 || !(mesh->hi > mesh->lo)) {
+    g_create_error = "create_mesh: order must be 2 or 4, ncell >= 1, hi > lo";
+    return INVDFT_EINVAL;
+  }
+  const long long Ni = (long long)mesh->ncell * mesh->order - 1;
+  if (Ni < 1 || Ni > 2047) {
+    g_create_error = "create_mesh: mesh has no unknowns or is too large";
+    return INVDFT_EINVAL;
+  }
+  if (opts->nstates < 1 || opts->nstates > kMaxDense) {
+    g_create_error = "create_mesh: nstates must be in [1, 96]";
+    return INVDFT_EINVAL;
+  }
+  invdft_ctx *c = new (std::nothrow) invdft_ctx();
+  if (!c) {
+    g_create_error = "create_mesh: out of host memory";
+    return INVDFT_ENOMEM;
+  }
+  c->mesh = *mesh;
+  c->o = *opts;
+  invdft_opts &o = c->o;
+  if (o.cheb_degree <= 0) o.cheb_degree = 20;
+  if (o.c_eig <= 0) o.c_eig = 1e2;
+  if (o.c_ad <= 0) o.c_ad = 1e5;
+  if (o.tau_bc <= 0) o.tau_bc = 1e-6;
+  if (o.max_cheb_passes <= 0) o.max_cheb_passes = 60;
+  if (o.max_minres_iters <= 0) o.max_minres_iters = 2000;
+  if (o.lbfgs_history <= 0) o.lbfgs_history = 10;
+  if (o.deg_tol <= 0) o.deg_tol = 1e-8;
+  if (o.kT < 0) o.kT = 0;
+  c->nv = o.nstates;
+  build_tables(mesh->lo, mesh->hi, mesh->ncell, mesh->order, &c->tab);
+  Geom &g = c->g;
+  g.p = mesh->order;
+  g.q = mesh->order + 1;
+  g.ncell = mesh->ncell;
+  g.Ni = (int)Ni;
+  g.L = Ni * Ni * Ni;
+  g.kc = 0.25 * (mesh->hi - mesh->lo) / mesh->ncell;
+  for (int i = 0; i < g.q * g.q; ++i) {
+    g.A[i] = c->tab.A[i];
+    g.B[i] = c->tab.B[i];
+  }
+  c->L = g.L;
+  c->ws_bytes = plan(c, nullptr);
+  *out = c;
+  if (n_nodes_out) *n_nodes_out = c->L;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_destroy(invdft_handle h) {
+  if (!h) return INVDFT_EINVAL;
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  delete h;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_workspace_size(invdft_handle h, size_t *bytes) {
+  if (!h || !bytes) return INVDFT_EINVAL;
+  *bytes = h->ws_bytes;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t bytes, void *stream) {
+  if (!h) return INVDFT_EINVAL;
+  if (!device_ptr || bytes < h->ws_bytes) {
+    h->err = "bind_workspace: workspace missing or smaller than invdft_workspace_size";
+    return INVDFT_ENOMEM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  char *base = reinterpret_cast<char *>(((uintptr_t)device_ptr + 255) & ~uintptr_t(255));
+  if ((size_t)(base - (char *)device_ptr) + h->ws_bytes - 256 > bytes) {
+    h->err = "bind_workspace: workspace too small after alignment";
+    return INVDFT_ENOMEM;
+  }
+  plan(h, base);
+  if (!h->hbuf) INV_CUDA(h, cudaHostAlloc((void **)&h->hbuf, 16 * kMaxCols * sizeof(double), 0));
+  // 1D tables: 1/sqrt(m1) (zero at the Dirichlet ends), m1, assembled diagonals
+  const int N = h->g.Ni + 2;
+  std::vector<double> dm1(N), tabs(3 * (size_t)N);
+  for (int i = 0; i < N; ++i) {
+    dm1[i] = (i == 0 || i == N - 1) ? 0.0 : 1.0 / std::sqrt(h->tab.m1[i]);
+    tabs[i] = h->tab.m1[i];
+    tabs[N + i] = h->tab.kdiag1_A[i];
+    tabs[2 * N + i] = h->tab.kdiag1_B[i];
+  }
+  double *m1 = h->m1tab, *kA = h->kAtab, *kB = h->kBtab;
+  INV_CUDA(h, cudaMemcpyAsync(h->dm1, dm1.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  INV_CUDA(h, cudaMemcpyAsync(m1, tabs.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  INV_CUDA(h, cudaMemcpyAsync(kA, tabs.data() + N, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  INV_CUDA(h, cudaMemcpyAsync(kB, tabs.data() + 2 * N, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag);
+  INV_LAUNCH(h, "init_fields");
+  INV_CUDA(h, cudaMemsetAsync(h->v, 0, h->L * sizeof(double), s));
+  INV_CUDA(h, cudaMemsetAsync(h->vfixed, 0, h->L * sizeof(double), s));
+  INV_CUDA(h, cudaStreamSynchronize(s));   // host tables above are freed on return
+  h->g.dm1 = h->dm1;
+  h->bound = true;
+  h->have_potential = false;
+  h->have_orbitals = false;
+  h->have_forward = false;
+  h->have_grad = false;
+  h->have_upper = false;
+  h->hist_n = h->hist_head = 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_node_coords(invdft_handle h, double *xyz) {
+  if (!h || !xyz) return INVDFT_EINVAL;
+  const int Ni = h->g.Ni;
+  const std::vector<double> &ax = h->tab.axis;
+  long long a = 0;
+  for (int iz = 1; iz <= Ni; ++iz)
+    for (int iy = 1; iy <= Ni; ++iy)
+      for (int ix = 1; ix <= Ni; ++ix, ++a) {
+        xyz[3 * a + 0] = ax[ix];
+        xyz[3 * a + 1] = ax[iy];
+        xyz[3 * a + 2] = ax[iz];
+      }
+  return INVDFT_OK;
+}
+
+invdft_status invdft_mass_diag(invdft_handle h, double *m_dev, void *stream) {
+  if (!h || !m_dev) return INVDFT_EINVAL;
+  if (!h->bound) {
+    h->err = "mass_diag: bind a workspace first";
+    return INVDFT_ENOMEM;
+  }
+  INV_CUDA(h, cudaMemcpyAsync(m_dev, h->mass, h->L * sizeof(double), cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+  return INVDFT_OK;
+}
+
+invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed, const double *v_xc,
+                                   void *stream) {
+  if (!h || !v_fixed) return INVDFT_EINVAL;
+  if (!h->bound) {
+    h->err = "set_potential: bind a workspace first";
+    return INVDFT_ENOMEM;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  INV_CUDA(h, cudaMemcpyAsync(h->vfixed, v_fixed, h->L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  add_fields<<<grid_for(h->L), 256, 0, s>>>(v_fixed, v_xc, h->v, h->L);
+  INV_LAUNCH(h, "add_fields");
+  h->have_potential = true;
+  h->have_forward = false;
+  h->have_grad = false;
+  h->have_upper = false;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_apply_h(invdft_handle h, const void *X, void *Y, int ncol,
+                             invdft_precision prec, void *stream) {
+  if (!h || !X || !Y || ncol < 1 || ncol > kMaxCols || X == Y) {
+    if (h) h->err = "apply_h: bad arguments (ncol in [1,256], X != Y)";
+    return INVDFT_EINVAL;
+  }
+  if (!h->bound || !h->have_potential) {
+    h->err = "apply_h: bind a workspace and set a potential first";
+    return INVDFT_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (prec == INVDFT_FP64) {
+    HxArgs<double> a;
+    a.X = (const double *)X;
+    a.Z = (double *)Y;
+    a.ncol = ncol;
+    e = launch_hx(h->g, h->v, a, s);
+  } else {
+    HxArgs<float> a;
+    a.X = (const float *)X;
+    a.Z = (float *)Y;
+    a.ncol = ncol;
+    e = launch_hx(h->g, h->v, a, s);
+  }
+  if (!cuda_ok(h, e, "apply_h")) return INVDFT_ECUDA;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_chebyshev_filter(invdft_handle h, const void *X, void *Y, int ncol, int degree,
+                                      double a, double b, double a0, invdft_precision prec,
+                                      void *stream) {
+  if (!h || !X || !Y || ncol < 1 || ncol > h->nv || degree < 1 || !(b > a) || !(a0 < a)) {
+    if (h) h->err = "chebyshev_filter: bad arguments (ncol <= nstates, b > a > a0)";
+    return INVDFT_EINVAL;
+  }
+  if (!h->bound || !h->have_potential) {
+    h->err = "chebyshev_filter: bind a workspace and set a potential first";
+    return INVDFT_EINVAL;
+  }
+  return run_filter(h, X, Y, ncol, degree, a, b, a0, prec, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+invdft_status invdft_reset(invdft_handle h) {
+  if (!h) return INVDFT_EINVAL;
+  h->have_orbitals = false;
+  h->have_forward = false;
+  h->have_grad = false;
+  h->have_upper = false;
+  h->hist_n = h->hist_head = 0;
+  return INVDFT_OK;
+}
+
+const char *invdft_last_error(invdft_handle h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+// H~X: the finite-element Hamiltonian in standard form applied to a block of
+// vectors, cell by cell (Sec. 3.2.3, Eq. 17, Eq. 19).
+//
+//   Z = alpha * (D K D X + (v - shift) o X) + beta * W + alpha * E diag(escale)
+//
+// Two launches: a nodal pass writes everything but the kinetic term, then the
+// cell pass gathers X_e (scaled by d = m^-1/2) for each cell, applies the
+// dense cell matrix K_e in its Kronecker-factored form and scatter-adds
+// d o (K_e X_e) into Z.  K_e = kc (B(x)B(x)A + B(x)A(x)B + A(x)B(x)B) is the
+// exact dense 125x125 (Q4) matrix; applying it as seven 1D contractions of the
+// (p+1)^3 cell tensor gives the same product with 3.5x fewer FP64 operations,
+// which matters because FP64 is the scarce pipe on this part.
+#include "internal.h"
+
+namespace invdft {
+namespace {
+
+template <typename T>
+__global__ void hx_nodal(const T *__restrict__ X, T *__restrict__ Z, const double *__restrict__ v,
+                         long long L, int ncol, double alpha, double shift,
+                         const double *__restrict__ shift_col, const T *__restrict__ W, double beta,
+                         const float *__restrict__ E, const double *__restrict__ escale) {
+  const long long n = L * (long long)ncol;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long a = i / ncol;
+    const int j = (int)(i - a * ncol);
+    const double sh = shift_col ? shift_col[j] : shift;
+    double z = alpha * (v[a] - sh) * (double)X[i];
+    if (W) z += beta * (double)W[i];
+    if (E) z += alpha * escale[j] * (double)E[i];
+    Z[i] = (T)z;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void atomic_add(T *p, T x) { atomicAdd(p, x); }
+
+// One CTA per (cell, chunk of C columns).  Two shared buffers of (p+1)^3 x C.
+template <typename T, int P, int C>
+__global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__restrict__ Z,
+                                                int ncol, Geom g, double scale) {
+  constexpr int Q = P + 1, NE = Q * Q * Q;
+  extern __shared__ unsigned char smem_raw[];
+  T *u = reinterpret_cast<T *>(smem_raw);
+  T *w = u + NE * C;
+  __shared__ T sA[Q * Q], sB[Q * Q];
+  __shared__ double dl[3][Q];
+  __shared__ int gidx[3][Q];
+
+  const int nc = g.ncell, Ni = g.Ni;
+  const int cell = blockIdx.x;
+  const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+  const int c0 = blockIdx.y * C;
+  const int tid = threadIdx.x;
+
+  if (tid < Q * Q) {
+    sA[tid] = (T)g.A[tid];
+    sB[tid] = (T)g.B[tid];
+  }
+  if (tid < 3 * Q) {
+    const int d = tid / Q, l = tid % Q;
+    const int c = d == 0 ? cx : (d == 1 ? cy : cz);
+    const int gi = c * P + l;                 // full-grid index along the axis
+    dl[d][l] = g.dm1[gi];                     // 0 on the boundary
+    gidx[d][l] = (gi >= 1 && gi <= Ni) ? gi - 1 : -1;
+  }
+  __syncthreads();
+
+  // gather: u[a][j] = d_a X[node(a)][c0 + j]
+  for (int idx = tid; idx < NE * C; idx += blockDim.x) {
+    const int a = idx / C, j = idx - a * C;
+    const int lx = a % Q, ly = (a / Q) % Q, lz = a / (Q * Q);
+    const int ix = gidx[0][lx], iy = gidx[1][ly], iz = gidx[2][lz];
+    T val = (T)0;
+    if (ix >= 0 && iy >= 0 && iz >= 0 && c0 + j < ncol) {
+      const long long node = ix + (long long)Ni * (iy + (long long)Ni * iz);
+      val = (T)(dl[0][lx] * dl[1][ly] * dl[2][lz]) * X[node * ncol + c0 + j];
+    }
+    u[idx] = val;
+  }
+  __syncthreads();
+
+  // x lines: u <- B_x u, w <- A_x u
+  for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
+    const int j = idx % C, line = idx / C;
+    const int base = line * Q;
+    T in[Q];
+#pragma unroll
+    for (int x = 0; x < Q; ++x) in[x] = u[(base + x) * C + j];
+#pragma unroll
+    for (int xo = 0; xo < Q; ++xo) {
+      T sb = 0, sa = 0;
+#pragma unroll
+      for (int x = 0; x < Q; ++x) {
+        sb += sB[xo * Q + x] * in[x];
+        sa += sA[xo * Q + x] * in[x];
+      }
+      u[(base + xo) * C + j] = sb;
+      w[(base + xo) * C + j] = sa;
+    }
+  }
+  __syncthreads();
+
+  // y lines: u <- B_y u (= B_y B_x X), w <- A_y u + B_y w (= A_y B_x X + B_y A_x X)
+  for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
+    const int j = idx % C, r = idx / C;
+    const int x = r % Q, z = r / Q;
+    T t1[Q], t2[Q];
+#pragma unroll
+    for (int y = 0; y < Q; ++y) {
+      t1[y] = u[(x + Q * (y + Q * z)) * C + j];
+      t2[y] = w[(x + Q * (y + Q * z)) * C + j];
+    }
+#pragma unroll
+    for (int yo = 0; yo < Q; ++yo) {
+      T s11 = 0, q = 0;
+#pragma unroll
+      for (int y = 0; y < Q; ++y) {
+        s11 += sB[yo * Q + y] * t1[y];
+        q += sA[yo * Q + y] * t1[y] + sB[yo * Q + y] * t2[y];
+      }
+      u[(x + Q * (yo + Q * z)) * C + j] = s11;
+      w[(x + Q * (yo + Q * z)) * C + j] = q;
+    }
+  }
+  __syncthreads();
+
+  // z lines: u <- A_z u + B_z w
+  for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
+    const int j = idx % C, r = idx / C;
+    const int x = r % Q, y = r / Q;
+    T t1[Q], t2[Q];
+#pragma unroll
+    for (int z = 0; z < Q; ++z) {
+      t1[z] = u[(x + Q * (y + Q * z)) * C + j];
+      t2[z] = w[(x + Q * (y + Q * z)) * C + j];
+    }
+#pragma unroll
+    for (int zo = 0; zo < Q; ++zo) {
+      T s = 0;
+#pragma unroll
+      for (int z = 0; z < Q; ++z) s += sA[zo * Q + z] * t1[z] + sB[zo * Q + z] * t2[z];
+      u[(x + Q * (y + Q * zo)) * C + j] = s;
+    }
+  }
+  __syncthreads();
+
+  // scatter-add d_a * scale * (K_e X_e)_a
+  for (int idx = tid; idx < NE * C; idx += blockDim.x) {
+    const int a = idx / C, j = idx - a * C;
+    const int lx = a % Q, ly = (a / Q) % Q, lz = a / (Q * Q);
+    const int ix = gidx[0][lx], iy = gidx[1][ly], iz = gidx[2][lz];
+    if (ix >= 0 && iy >= 0 && iz >= 0 && c0 + j < ncol) {
+      const long long node = ix + (long long)Ni * (iy + (long long)Ni * iz);
+      const T val = (T)(scale * dl[0][lx] * dl[1][ly] * dl[2][lz]) * u[idx];
+      atomic_add(&Z[node * ncol + c0 + j], val);
+    }
+  }
+}
+
+template <typename T, int P, int C>
+cudaError_t run_cells(const Geom &g, const T *X, T *Z, int ncol, double scale, cudaStream_t s) {
+  constexpr int Q = P + 1, NE = Q * Q * Q;
+  const size_t smem = 2 * (size_t)NE * C * sizeof(T);
+  auto k = hx_cells<T, P, C>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.ncell * g.ncell * g.ncell, (ncol + C - 1) / C);
+  k<<<grid, 256, smem, s>>>(X, Z, ncol, g, scale);
+  return cudaGetLastError();
+}
+
+template <typename T, int P>
+cudaError_t run_cells_p(const Geom &g, const T *X, T *Z, int ncol, double scale, cudaStream_t s) {
+  if (ncol <= 8) return run_cells<T, P, 8>(g, X, Z, ncol, scale, s);
+  if (ncol <= 16) return run_cells<T, P, 16>(g, X, Z, ncol, scale, s);
+  return run_cells<T, P, 32>(g, X, Z, ncol, scale, s);
+}
+
+template <typename T>
+cudaError_t launch_hx_t(const Geom &g, const double *v, const HxArgs<T> &a, cudaStream_t s) {
+  if (a.ncol < 1 || a.ncol > kMaxCols) return cudaErrorInvalidValue;
+  const long long n = g.L * a.ncol;
+  int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  hx_nodal<T><<<blocks, 256, 0, s>>>(a.X, a.Z, v, g.L, a.ncol, a.alpha, a.shift, a.shift_col, a.W,
+                                     a.beta, a.E, a.escale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const double scale = a.alpha * g.kc;
+  if (g.p == 2) return run_cells_p<T, 2>(g, a.X, a.Z, a.ncol, scale, s);
+  if (g.p == 4) return run_cells_p<T, 4>(g, a.X, a.Z, a.ncol, scale, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<double> &a, cudaStream_t s) {
+  return launch_hx_t<double>(g, v, a, s);
+}
+cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cudaStream_t s) {
+  return launch_hx_t<float>(g, v, a, s);
+}
+
+}  // namespace invdft

@@ -1,0 +1,163 @@
+// Internal declarations of libinvdft: the handle, device-table layout and the
+// launchers of every kernel.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/invdft.h"
+
+namespace invdft {
+
+constexpr int kMaxOrder = 4;
+constexpr int kMaxQ = kMaxOrder + 1;
+constexpr int kMaxCols = 256;       // widest block H~X accepts
+constexpr int kMaxGram = 128;       // widest block of Gram / rotation work
+constexpr int kMaxDense = 96;       // widest subspace of the one-CTA dense eigensolver
+constexpr int kMaxGroup = 16;       // largest degenerate set handled by the projections
+constexpr int kGramBlocks = 296;    // 2 x 148 SMs: partial sums of tall-skinny reductions
+
+// Geometry and 1D factors of the cell operator, passed to kernels by value.
+// K_e = kc * (B (x) B (x) A + B (x) A (x) B + A (x) B (x) B)  (z, y, x order),
+// kc = h/4, with A, B the 1D GLL stiffness and consistent mass on [-1, 1].
+struct Geom {
+  int p, q, ncell, Ni;      // order, nodes per cell edge, cells per axis, unknowns per axis
+  long long L;              // unknowns
+  double kc;
+  double A[kMaxQ * kMaxQ];
+  double B[kMaxQ * kMaxQ];
+  const double *dm1;        // device [Ni + 2]: 1/sqrt(m1) along one axis (0 at the ends)
+};
+
+// Host-side FE tables (tables.cu).
+struct Tables {
+  std::vector<double> gll_x, gll_w;   // q
+  std::vector<double> A, B;           // q x q
+  std::vector<double> axis;           // node coordinates along one axis, Ni + 2
+  std::vector<double> m1;             // 1D lumped mass, Ni + 2
+  std::vector<double> kdiag1_A, kdiag1_B;  // assembled 1D diagonals (for the preconditioner)
+};
+void build_tables(double lo, double hi, int ncell, int p, Tables *t);
+
+// Bump allocator over the caller's workspace.
+struct Arena {
+  char *base = nullptr;
+  size_t cap = 0, off = 0;
+  template <class T> T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = reinterpret_cast<T *>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+struct Ctx {
+  invdft_mesh_desc mesh{};
+  invdft_opts o{};
+  Tables tab;
+  Geom g{};
+  long long L = 0;
+  int nv = 0;                       // nstates
+  std::string err;
+  bool bound = false;
+  bool have_potential = false;
+  bool have_orbitals = false;       // warm start available
+  bool have_forward = false;        // eps/occ/psi of the last forward solve valid
+  size_t ws_bytes = 0;
+  Arena ar;
+  double upper_bound = 0.0;         // cached spectral upper bound of H~
+  bool have_upper = false;
+
+  // ---- device state (inside the workspace)
+  double *dm1 = nullptr;            // [Ni+2]
+  double *m1tab = nullptr, *kAtab = nullptr, *kBtab = nullptr;  // [Ni+2] 1D tables
+  double *mass = nullptr;           // [L]
+  double *dvec = nullptr;           // [L]  m^-1/2
+  double *prec_diag = nullptr;      // [L]  1 / diag(D K D)
+  double *v = nullptr;              // [L]  total potential
+  double *vfixed = nullptr;         // [L]
+  double *X = nullptr;              // [L][nv] orbitals (FP64)
+  double *Y = nullptr;              // [L][nv]
+  double *HY = nullptr;             // [L][nv]
+  void *C0 = nullptr, *C1 = nullptr, *C2 = nullptr;  // filter buffers [L][nv] (prec)
+  float *E32 = nullptr;             // [L][nv] residual copy for the defect-corrected filter
+  double *eps = nullptr, *occ = nullptr, *dfde = nullptr, *rho = nullptr;
+  double *small = nullptr;          // dense scratch: 8 * kMaxCols^2 doubles
+  double *partial = nullptr;        // kGramBlocks * kMaxCols^2 doubles
+  double *scal = nullptr;           // 1024 * kMaxCols doubles of per-column scalars and tables
+  int *status = nullptr;            // device status words [16]
+  // adjoint
+  double *P = nullptr;              // [L][nv] adjoint output (FP64)
+  double *Rg = nullptr;             // [L][nv] right-hand sides / residuals (FP64)
+  void *mr[9] = {};                 // MINRES work blocks [L][nv] (FP32 or FP64)
+  // inverse loop
+  double *grad = nullptr, *grad_new = nullptr, *dir = nullptr, *vtry = nullptr, *dLdrho = nullptr;
+  double *Sh = nullptr, *Yh = nullptr;   // [hist][L]
+  int hist_n = 0, hist_head = 0;
+  bool have_grad = false;
+  double loss = 0.0, err_l2 = 0.0;
+  // pinned host mirror for small read-backs
+  double *hbuf = nullptr;           // 16 * kMaxCols doubles
+};
+
+}  // namespace invdft
+
+// The opaque handle type of the C ABI is the context itself.
+struct invdft_ctx : public invdft::Ctx {};
+
+namespace invdft {
+
+// ------------------------------------------------------------ error helpers
+bool cuda_ok(Ctx *c, cudaError_t e, const char *what);
+#define INV_CUDA(c, call)                                   \
+  do {                                                      \
+    if (!::invdft::cuda_ok((c), (call), #call)) return INVDFT_ECUDA; \
+  } while (0)
+#define INV_LAUNCH(c, what)                                 \
+  do {                                                      \
+    if (!::invdft::cuda_ok((c), cudaGetLastError(), what)) return INVDFT_ECUDA; \
+  } while (0)
+
+// ------------------------------------------------------------ H~X (hx.cu)
+// Z = alpha * (H~ X - shift o X) + beta * W + alpha * E diag(escale)
+//   shift: per-column (shift_col != nullptr) or the scalar shift;
+//   W, E optional (nullptr); escale per column (device) for E.
+template <typename T>
+struct HxArgs {
+  const T *X = nullptr;
+  T *Z = nullptr;
+  int ncol = 0;
+  double alpha = 1.0;
+  double shift = 0.0;
+  const double *shift_col = nullptr;
+  const T *W = nullptr;
+  double beta = 0.0;
+  const float *E = nullptr;
+  const double *escale = nullptr;
+};
+cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<double> &a, cudaStream_t s);
+cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cudaStream_t s);
+
+// ------------------------------------------------------------ vector kernels (blas.cu)
+// G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).
+cudaError_t launch_gram(const double *A, int n1, const double *B, int n2, long long L,
+                        double *G, double *partial, cudaStream_t s);
+cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long long L,
+                            double *G, double *partial, cudaStream_t s);
+// Xo[a][j] = sum_i Xi[a][i] Cm[i*n2 + j]   (n1 -> n2 columns), FP64
+cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, long long L,
+                          double *Xo, cudaStream_t s);
+// column-wise dot products d[j] = sum_a A[a][j] B[a][j] (FP64 accumulate)
+cudaError_t launch_coldot(const double *A, const double *B, int ncol, long long L, double *d,
+                          double *partial, cudaStream_t s);
+cudaError_t launch_coldot_f32(const float *A, const float *B, int ncol, long long L, double *d,
+                              double *partial, cudaStream_t s);
+// weighted scalar sums over nodes: out[k] = sum_a f_k(a) (see blas.cu)
+cudaError_t launch_convert_f64_to_f32(const double *x, float *y, long long n, cudaStream_t s);
+cudaError_t launch_convert_f32_to_f64(const float *x, double *y, long long n, cudaStream_t s);
+cudaError_t launch_fill_random(double *X, long long n, unsigned long long seed, cudaStream_t s);
+
+}  // namespace invdft

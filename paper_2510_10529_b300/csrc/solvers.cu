@@ -1,0 +1,858 @@
+// Host orchestration of the solvers (kernels run on the caller's stream):
+//   * Chebyshev filter (plain scaled recurrence; defect-corrected form for the
+//     mixed path) and Chebyshev-filtered subspace iteration with FP64
+//     Rayleigh-Ritz (Sec. 3.2.2, Eq. 23-24);
+//   * batched projected preconditioned MINRES for all occupied adjoint
+//     systems at once (Sec. 3.2.2), with FP64 iterative refinement;
+//   * loss + gradient and the L-BFGS iteration (Eq. 1, 11, 21, 22).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "solvers.h"
+
+namespace invdft {
+
+namespace {
+
+// Offsets (in doubles) inside the per-handle scalar area c->scal.
+constexpr size_t kScMisc = 0;                       // dots, loss sums
+constexpr size_t kScMu = 32;                        // chemical potential
+constexpr size_t kScRes = 64;                       // Ritz residual norms^2 [nv]
+constexpr size_t kScCol = 512;                      // column dots [<= 256]
+constexpr size_t kScAdj = 200 * (size_t)kMaxCols;   // adjoint per-column tables
+constexpr size_t kScMr = 256 * (size_t)kMaxCols;    // MINRES scalars
+constexpr size_t kScInt = 400 * (size_t)kMaxCols;   // adjoint int tables
+constexpr size_t kScPk = 512 * (size_t)kMaxCols;    // Chebyshev p_k(theta) table
+
+// per-column MINRES scalars, st[k * n + c]
+enum { kMrAlpha = 0, kMrBeta, kMrBnext, kMrCpp, kMrSpp, kMrCp, kMrSp, kMrPhibar, kMrBeta1,
+       kMrActive, kMrEps, kMrDel, kMrIg, kMrT, kMrIb, kMrRel, kMrTol, kMrIters, kMrCount };
+
+double wall_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+invdft_status fetch(Ctx *c, const void *dev, size_t bytes, void *host, cudaStream_t s) {
+  if (bytes > 16 * kMaxCols * sizeof(double)) {
+    INV_CUDA(c, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+    INV_CUDA(c, cudaStreamSynchronize(s));
+    return INVDFT_OK;
+  }
+  INV_CUDA(c, cudaMemcpyAsync(c->hbuf, dev, bytes, cudaMemcpyDeviceToHost, s));
+  INV_CUDA(c, cudaStreamSynchronize(s));
+  std::memcpy(host, c->hbuf, bytes);
+  return INVDFT_OK;
+}
+
+invdft_status push(Ctx *c, void *dev, const void *host, size_t bytes, cudaStream_t s) {
+  // synchronous w.r.t. the host buffer: the stream is synchronised before reuse
+  INV_CUDA(c, cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s));
+  INV_CUDA(c, cudaStreamSynchronize(s));
+  return INVDFT_OK;
+}
+
+#define TRY(x)                             \
+  do {                                     \
+    invdft_status _st = (x);               \
+    if (_st != INVDFT_OK) return _st;      \
+  } while (0)
+#define CU(x, what)                                             \
+  do {                                                          \
+    if (!cuda_ok(c, (x), what)) return INVDFT_ECUDA;            \
+  } while (0)
+
+// Largest eigenvalue of a symmetric tridiagonal matrix by Sturm bisection.
+double tridiag_max_eig(const std::vector<double> &d, const std::vector<double> &e) {
+  const int k = (int)d.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < k - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto count_below = [&](double x) {       // number of eigenvalues < x
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < k; ++i) {
+      const double qq = (q == 0.0) ? 1e-300 : q;
+      q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-12 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= k) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Upper bound of the spectrum of H~: k-step Lanczos, max Ritz value + |f|.
+invdft_status upper_bound(Ctx *c, cudaStream_t s, double *out) {
+  const long long L = c->L;
+  double *v0 = (double *)c->C0, *v = (double *)c->C1, *f = (double *)c->C2, *sc = c->scal + kScMisc;
+  CU(launch_fill_random(v, L, c->o.seed ^ 0xA5A5A5A5ULL, s), "fill_random");
+  CU(launch_dot(v, v, L, sc, c->partial, s), "dot");
+  double nrm;
+  TRY(fetch(c, sc, sizeof(double), &nrm, s));
+  CU(launch_axpby(0.0, v, 1.0 / std::sqrt(nrm), v, L, s), "axpby");
+  CU(cudaMemsetAsync(v0, 0, L * sizeof(double), s), "memset");
+  const int k = 12;
+  std::vector<double> d, e;
+  double beta = 0.0;
+  for (int j = 0; j < k; ++j) {
+    HxArgs<double> a;
+    a.X = v;
+    a.Z = f;
+    a.ncol = 1;
+    a.W = v0;
+    a.beta = -beta;                  // f = H v - beta v0
+    CU(launch_hx(c->g, c->v, a, s), "hx(lanczos)");
+    CU(launch_dot(f, v, L, sc, c->partial, s), "dot");
+    double alpha;
+    TRY(fetch(c, sc, sizeof(double), &alpha, s));
+    CU(launch_axpby(-alpha, v, 1.0, f, L, s), "axpby");
+    CU(launch_dot(f, f, L, sc, c->partial, s), "dot");
+    double ff;
+    TRY(fetch(c, sc, sizeof(double), &ff, s));
+    d.push_back(alpha);
+    beta = std::sqrt(std::max(ff, 0.0));
+    if (j < k - 1) {
+      e.push_back(beta);
+      std::swap(v0, v);                         // v0 <- v
+      CU(launch_lincomb(1.0 / beta, f, 0.0, f, v, L, s), "lincomb");   // v <- f / beta
+    }
+  }
+  e.resize(d.size() - 1);
+  *out = tridiag_max_eig(d, e) + beta;
+  return INVDFT_OK;
+}
+
+// Rayleigh-Ritz on (Y, HY): X = Y C, E = (HY C) - X diag(theta) (kept in Y,
+// FP64) and E32; theta in c->eps.  Residual norms^2 of the Ritz pairs in
+// c->scal[64 .. 64+nv).
+invdft_status rayleigh_ritz(Ctx *c, cudaStream_t s) {
+  const int n = c->nv;
+  const long long L = c->L;
+  double *S = c->small, *Hs = c->small + kMaxGram * kMaxGram, *Cm = c->small + 2 * kMaxGram * kMaxGram;
+  double *work = c->small + 3 * kMaxGram * kMaxGram;
+  CU(launch_gram(c->Y, n, c->Y, n, L, S, c->partial, s), "gram(S)");
+  CU(launch_gram(c->Y, n, c->HY, n, L, Hs, c->partial, s), "gram(H)");
+  CU(launch_rr_small(S, Hs, n, c->eps, Cm, c->status, work, s), "rr_small");
+  int st = 0;
+  TRY(fetch(c, c->status, sizeof(int), &st, s));
+  if (st != 0) {
+    c->err = "Rayleigh-Ritz: the filtered block is numerically rank deficient (Cholesky failed)";
+    return INVDFT_ENOTSPD;
+  }
+  CU(launch_rotate(c->Y, n, Cm, n, L, c->X, s), "rotate(X)");
+  CU(launch_rotate(c->HY, n, Cm, n, L, c->Y, s), "rotate(HX)");
+  CU(launch_residual_block(c->Y, c->X, c->eps, n, L, c->Y, c->E32, s), "residual");
+  CU(launch_coldot(c->Y, c->Y, n, L, c->scal + kScRes, c->partial, s), "coldot(res)");
+  return INVDFT_OK;
+}
+
+invdft_status apply_h_f64(Ctx *c, const double *X, double *Z, int n, cudaStream_t s) {
+  HxArgs<double> a;
+  a.X = X;
+  a.Z = Z;
+  a.ncol = n;
+  CU(launch_hx(c->g, c->v, a, s), "hx");
+  return INVDFT_OK;
+}
+
+double eig_tolerance(const Ctx *c) {
+  if (c->o.eig_tol > 0) return c->o.eig_tol;
+  if (c->err_l2 <= 0) return 1e-6;
+  return std::min(1e-3, std::max(c->err_l2 * c->err_l2 / c->o.c_eig, 1e-10));
+}
+double adj_tolerance(const Ctx *c) {
+  if (c->o.adj_tol > 0) return c->o.adj_tol;
+  if (c->err_l2 <= 0) return 1e-8;
+  return std::min(1e-4, std::max(c->err_l2 * c->err_l2 / c->o.c_ad, 1e-10));
+}
+
+bool state_active(const Ctx *c, double f) { return c->o.kT > 0 ? f > 1e-13 : f > 0.0; }
+
+}  // namespace
+
+invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double a, double b,
+                         double a0, invdft_precision prec, const double *theta, const float *E,
+                         cudaStream_t s) {
+  const double e = 0.5 * (b - a), cc = 0.5 * (b + a);
+  const double sigma1 = e / (a0 - cc);
+  void *bufs[3] = {c->C0, c->C1, c->C2};
+  auto free_buf = [&](const void *p1, const void *p2) -> void * {
+    for (void *q : bufs)
+      if (q != p1 && q != p2) return q;
+    return nullptr;
+  };
+  if (theta == nullptr) {
+    const void *prev = nullptr, *cur = X;
+    double sigma = sigma1;
+    for (int k = 1; k <= m; ++k) {
+      const double sn = (k == 1) ? sigma1 : 1.0 / (2.0 / sigma1 - sigma);
+      void *Z = (k == m) ? Y : free_buf(prev, cur);
+      const double alpha = (k == 1) ? sigma1 / e : 2.0 * sn / e;
+      const double beta = (k == 1) ? 0.0 : -sigma * sn;
+      cudaError_t err;
+      if (prec == INVDFT_FP64) {
+        HxArgs<double> h;
+        h.X = (const double *)cur;
+        h.Z = (double *)Z;
+        h.ncol = ncol;
+        h.alpha = alpha;
+        h.shift = cc;
+        h.W = (const double *)prev;
+        h.beta = beta;
+        err = launch_hx(c->g, c->v, h, s);
+      } else {
+        HxArgs<float> h;
+        h.X = (const float *)cur;
+        h.Z = (float *)Z;
+        h.ncol = ncol;
+        h.alpha = alpha;
+        h.shift = cc;
+        h.W = (const float *)prev;
+        h.beta = beta;
+        err = launch_hx(c->g, c->v, h, s);
+      }
+      CU(err, "hx(filter)");
+      prev = cur;
+      cur = Z;
+      if (k > 1) sigma = sn;
+    }
+    return INVDFT_OK;
+  }
+  // defect-corrected filter: Y = X diag(p_m(theta)) + D_m, D in FP32
+  const int nk = m + 1;
+  if ((size_t)nk * ncol > 128 * (size_t)kMaxCols) {
+    c->err = "chebyshev filter: degree too high for the coefficient table";
+    return INVDFT_EINVAL;
+  }
+  std::vector<double> pk((size_t)nk * ncol);
+  std::vector<double> sig(nk + 1, 0.0);
+  sig[1] = sigma1;
+  for (int k = 1; k < m; ++k) sig[k + 1] = 1.0 / (2.0 / sigma1 - sig[k]);
+  for (int j = 0; j < ncol; ++j) {
+    double pm1 = 1.0, p = (sigma1 / e) * (theta[j] - cc);
+    pk[j] = 1.0;
+    if (m >= 1) pk[(size_t)ncol + j] = p;
+    for (int k = 1; k < m; ++k) {
+      const double pn = (2.0 * sig[k + 1] / e) * (theta[j] - cc) * p - sig[k] * sig[k + 1] * pm1;
+      pm1 = p;
+      p = pn;
+      pk[(size_t)(k + 1) * ncol + j] = p;
+    }
+  }
+  double *dpk = c->scal + kScPk;
+  TRY(push(c, dpk, pk.data(), pk.size() * sizeof(double), s));
+  const long long L = c->L;
+  float *D1 = (float *)c->C0;
+  CU(launch_scale_f32(E, nullptr, sigma1 / e, ncol, L, D1, s), "scale(D1)");
+  const void *prev = nullptr, *cur = D1;
+  for (int k = 2; k <= m; ++k) {
+    const double sn = sig[k];
+    void *Z = free_buf(prev, cur);
+    HxArgs<float> h;
+    h.X = (const float *)cur;
+    h.Z = (float *)Z;
+    h.ncol = ncol;
+    h.alpha = 2.0 * sn / e;
+    h.shift = cc;
+    h.W = (const float *)prev;
+    h.beta = prev ? -sig[k - 1] * sn : 0.0;
+    h.E = E;
+    h.escale = dpk + (size_t)(k - 1) * ncol;
+    CU(launch_hx(c->g, c->v, h, s), "hx(defect filter)");
+    prev = cur;
+    cur = Z;
+  }
+  CU(launch_cheb_combine((const double *)X, dpk + (size_t)m * ncol, (const float *)cur, ncol, L,
+                         (double *)Y, s),
+     "cheb_combine");
+  return INVDFT_OK;
+}
+
+// ---------------------------------------------------------------- forward
+invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
+  const double t0 = wall_ms();
+  const int n = c->nv;
+  const long long L = c->L;
+  const size_t blk = (size_t)L * n;
+  int hx_calls = 0;
+  if (!c->have_orbitals) {
+    CU(launch_fill_random(c->Y, (long long)blk, c->o.seed, s), "fill_random");
+    TRY(apply_h_f64(c, c->Y, c->HY, n, s));
+    ++hx_calls;
+    TRY(rayleigh_ritz(c, s));
+    c->have_orbitals = true;
+  } else {
+    CU(cudaMemcpyAsync(c->Y, c->X, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    TRY(apply_h_f64(c, c->Y, c->HY, n, s));
+    ++hx_calls;
+    TRY(rayleigh_ritz(c, s));
+  }
+  if (!c->have_upper) {
+    TRY(upper_bound(c, s, &c->upper_bound));
+    hx_calls += 12;
+    c->have_upper = true;
+  }
+  const double tol = eig_tolerance(c);
+  std::vector<double> theta(n), occ(n), res2(n);
+  int pass = 0;
+  double maxres = 0.0;
+  invdft_status status = INVDFT_OK;
+  for (;;) {
+    CU(launch_occupations(c->eps, n, c->o.n_electrons, c->o.kT, c->occ, c->dfde, c->scal + kScMu,
+                          c->status, s), "occupations");
+    TRY(fetch(c, c->eps, n * sizeof(double), theta.data(), s));
+    TRY(fetch(c, c->occ, n * sizeof(double), occ.data(), s));
+    TRY(fetch(c, c->scal + kScRes, n * sizeof(double), res2.data(), s));
+    int occ_status = 0;
+    TRY(fetch(c, c->status + 1, sizeof(int), &occ_status, s));
+    if (occ_status) {
+      c->err = "occupations: kT = 0 needs an even electron count and nstates > N_e/2";
+      return INVDFT_EINVAL;
+    }
+    maxres = 0.0;
+    for (int i = 0; i < n; ++i)
+      if (state_active(c, occ[i])) maxres = std::max(maxres, std::sqrt(std::max(res2[i], 0.0)));
+    if (maxres <= tol && pass >= 1) break;
+    if (pass >= c->o.max_cheb_passes) {
+      status = INVDFT_ENOCONV;
+      c->err = "forward solve: Chebyshev pass cap reached";
+      break;
+    }
+    const double a = theta[n - 1], a0 = theta[0];
+    double b = c->upper_bound;
+    if (!(b > a)) b = a + std::max(1.0, std::fabs(a));
+    if (c->o.prec == INVDFT_FP64) {
+      TRY(run_filter(c, c->X, c->Y, n, c->o.cheb_degree, a, b, a0, INVDFT_FP64, nullptr, nullptr, s));
+    } else {
+      TRY(run_filter(c, c->X, c->Y, n, c->o.cheb_degree, a, b, a0, INVDFT_MIXED, theta.data(),
+                     c->E32, s));
+    }
+    hx_calls += c->o.cheb_degree;
+    TRY(apply_h_f64(c, c->Y, c->HY, n, s));
+    ++hx_calls;
+    TRY(rayleigh_ritz(c, s));
+    ++pass;
+  }
+  CU(launch_density(c->X, n, c->occ, c->mass, L, c->rho, s), "density");
+  c->have_forward = true;
+  if (stats) {
+    stats->cheb_passes += pass;
+    stats->hx_calls += hx_calls;
+    stats->eig_resid_max = maxres;
+    double mu = 0.0;
+    TRY(fetch(c, c->scal + kScMu, sizeof(double), &mu, s));
+    stats->mu = mu;
+    stats->t_forward_ms += wall_ms() - t0;
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------- adjoint
+namespace {
+
+struct AdjPlan {
+  int no = 0;
+  std::vector<int> idx;        // compact column -> state
+  std::vector<int> cs, ia, ib; // pairs per column: [cs[c], cs[c+1])
+  int *d_idx = nullptr, *d_cs = nullptr, *d_ia = nullptr, *d_ib = nullptr;
+  double *d_eps_o = nullptr, *d_f_o = nullptr, *d_dcoef = nullptr, *d_coef = nullptr;
+};
+
+template <typename T>
+invdft_status project(Ctx *c, const AdjPlan &pl, const double *Psi_o, T *X, cudaStream_t s) {
+  const int np = pl.cs[pl.no];
+  CU((launch_pairdot<double, T>(Psi_o, pl.no, pl.d_ia, X, pl.no, pl.d_ib, np, c->L, pl.d_coef,
+                                c->partial, s)), "pairdot");
+  CU(launch_project_apply<T>(Psi_o, pl.no, pl.d_cs, pl.d_ia, pl.d_coef, X, pl.no, c->L, s),
+     "project");
+  return INVDFT_OK;
+}
+
+template <typename T>
+invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const T *b, T *x,
+                           const std::vector<double> &tol, int maxit, int *iters_out,
+                           cudaStream_t s) {
+  const int n = pl.no;
+  const long long L = c->L;
+  const size_t blk = (size_t)L * n;
+  T *qprev = (T *)c->mr[0], *q = (T *)c->mr[1], *z = (T *)c->mr[2], *wpp = (T *)c->mr[3];
+  T *wp = (T *)c->mr[4], *p = (T *)c->mr[5], *zh = (T *)c->mr[6];
+  double *st = c->scal + kScMr;    // kMrCount x n scalars
+  CU(launch_prec_apply<T>(b, c->prec_diag, n, L, z, s), "prec");
+  TRY(project<T>(c, pl, Psi_o, z, s));
+  // beta1^2 into st[kMrBnext] temporarily
+  if (sizeof(T) == 8)
+    CU(launch_coldot((const double *)b, (const double *)z, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
+  else
+    CU(launch_coldot_f32((const float *)b, (const float *)z, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
+  std::vector<double> h((size_t)kMrCount * n, 0.0);
+  TRY(fetch(c, st + kMrBeta1 * n, n * sizeof(double), h.data() + kMrBeta1 * n, s));
+  for (int j = 0; j < n; ++j) {
+    const double b1 = std::sqrt(std::max(h[kMrBeta1 * n + j], 0.0));
+    h[kMrBeta1 * n + j] = b1;
+    h[kMrPhibar * n + j] = b1;
+    h[kMrActive * n + j] = b1 > 0.0 ? 1.0 : 0.0;
+    h[kMrCpp * n + j] = 1.0;
+    h[kMrCp * n + j] = 1.0;
+    h[kMrTol * n + j] = tol[j];
+    h[kMrRel * n + j] = b1 > 0.0 ? 1.0 : 0.0;
+  }
+  TRY(push(c, st, h.data(), h.size() * sizeof(double), s));
+  CU(launch_mr_init<T>(b, z, st + kMrBeta1 * n, n, L, q, z, s), "mr_init");
+  CU(cudaMemsetAsync(qprev, 0, blk * sizeof(T), s), "memset");
+  CU(cudaMemsetAsync(wpp, 0, blk * sizeof(T), s), "memset");
+  CU(cudaMemsetAsync(wp, 0, blk * sizeof(T), s), "memset");
+  CU(cudaMemsetAsync(x, 0, blk * sizeof(T), s), "memset");
+  int it = 0;
+  std::vector<double> act(n);
+  for (; it < maxit; ++it) {
+    if (it % 4 == 0 || it < 4) {
+      TRY(fetch(c, st + kMrActive * n, n * sizeof(double), act.data(), s));
+      bool any = false;
+      for (int j = 0; j < n; ++j) any |= act[j] != 0.0;
+      if (!any) break;
+    }
+    HxArgs<T> a;
+    a.X = z;
+    a.Z = p;
+    a.ncol = n;
+    a.shift_col = pl.d_eps_o;
+    CU(launch_hx(c->g, c->v, a, s), "hx(minres)");
+    TRY(project<T>(c, pl, Psi_o, p, s));
+    if (sizeof(T) == 8)
+      CU(launch_coldot((const double *)z, (const double *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
+    else
+      CU(launch_coldot_f32((const float *)z, (const float *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
+    CU(launch_mr_lanczos<T>(p, q, qprev, st + kMrAlpha * n, st + kMrBeta * n, c->prec_diag, n, L,
+                            p, zh, s), "mr_lanczos");
+    TRY(project<T>(c, pl, Psi_o, zh, s));
+    if (sizeof(T) == 8)
+      CU(launch_coldot((const double *)p, (const double *)zh, n, L, st + kMrBnext * n, c->partial, s), "coldot");
+    else
+      CU(launch_coldot_f32((const float *)p, (const float *)zh, n, L, st + kMrBnext * n, c->partial, s), "coldot");
+    CU(launch_mr_givens(n, st, s), "mr_givens");
+    CU(launch_mr_update<T>(z, zh, qprev, p, wpp, wp, x, st, n, L, s), "mr_update");
+    std::swap(qprev, q);
+    std::swap(wpp, wp);
+  }
+  std::vector<double> itv(n);
+  TRY(fetch(c, st + kMrIters * n, n * sizeof(double), itv.data(), s));
+  int mx = 0;
+  for (int j = 0; j < n; ++j) mx = std::max(mx, (int)itv[j]);
+  *iters_out = mx;
+  return INVDFT_OK;
+}
+
+}  // namespace
+
+// Adjoint functions for the upstream dL/drho (device [L]) around the last
+// forward solve.  Output: compact P_o in c->P ([L][no]), Psi_o in c->HY, and
+// the compact map in *plan.  If p_full != nullptr, also the full [L][nv].
+invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft_stats *stats,
+                            AdjPlan *plan_out, cudaStream_t s);
+
+invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft_stats *stats,
+                            AdjPlan *plan_out, cudaStream_t s) {
+  const double t0 = wall_ms();
+  if (!c->have_forward) {
+    c->err = "adjoint_solve: no forward solve at the current potential";
+    return INVDFT_EINVAL;
+  }
+  const int nv = c->nv;
+  const long long L = c->L;
+  std::vector<double> eps(nv), f(nv), dfde(nv);
+  TRY(fetch(c, c->eps, nv * sizeof(double), eps.data(), s));
+  TRY(fetch(c, c->occ, nv * sizeof(double), f.data(), s));
+  TRY(fetch(c, c->dfde, nv * sizeof(double), dfde.data(), s));
+  AdjPlan pl;
+  for (int i = 0; i < nv; ++i)
+    if (state_active(c, f[i])) pl.idx.push_back(i);
+  pl.no = (int)pl.idx.size();
+  const int no = pl.no;
+  if (no == 0) {
+    c->err = "adjoint_solve: no occupied states";
+    return INVDFT_EINVAL;
+  }
+  // degenerate sets among the active states (ascending eigenvalues)
+  std::vector<int> grp(no);
+  int g = 0;
+  for (int k = 0; k < no; ++k) {
+    if (k > 0 && !(eps[pl.idx[k]] - eps[pl.idx[k - 1]] < c->o.deg_tol)) ++g;
+    grp[k] = g;
+  }
+  pl.cs.assign(no + 1, 0);
+  for (int k = 0; k < no; ++k) {
+    int cnt = 0;
+    for (int j = 0; j < no; ++j)
+      if (grp[j] == grp[k]) {
+        pl.ia.push_back(j);
+        pl.ib.push_back(k);
+        ++cnt;
+      }
+    if (cnt > kMaxGroup) {
+      c->err = "adjoint_solve: degenerate set larger than 16";
+      return INVDFT_EINVAL;
+    }
+    pl.cs[k + 1] = pl.cs[k] + cnt;
+  }
+  const int np = pl.cs[no];
+  // device tables in the int/scalar areas of the workspace
+  int *ibase = reinterpret_cast<int *>(c->scal + kScInt);
+  pl.d_idx = ibase;
+  pl.d_cs = ibase + kMaxDense;
+  pl.d_ia = ibase + 2 * kMaxDense + 1;
+  pl.d_ib = pl.d_ia + kMaxDense * kMaxGroup;
+  std::vector<int> ints(2 * kMaxDense + 1 + 2 * kMaxDense * kMaxGroup, 0);
+  std::copy(pl.idx.begin(), pl.idx.end(), ints.begin());
+  std::copy(pl.cs.begin(), pl.cs.end(), ints.begin() + kMaxDense);
+  std::copy(pl.ia.begin(), pl.ia.end(), ints.begin() + 2 * kMaxDense + 1);
+  std::copy(pl.ib.begin(), pl.ib.end(), ints.begin() + 2 * kMaxDense + 1 + kMaxDense * kMaxGroup);
+  TRY(push(c, ibase, ints.data(), ints.size() * sizeof(int), s));
+  double *dbase = c->scal + kScAdj;
+  pl.d_eps_o = dbase;
+  pl.d_f_o = dbase + kMaxDense;
+  pl.d_dcoef = dbase + 2 * kMaxDense;
+  pl.d_coef = dbase + 2 * kMaxDense + kMaxDense * kMaxGroup;
+  std::vector<double> eo(no), fo(no);
+  for (int k = 0; k < no; ++k) {
+    eo[k] = eps[pl.idx[k]];
+    fo[k] = f[pl.idx[k]];
+  }
+  TRY(push(c, pl.d_eps_o, eo.data(), no * sizeof(double), s));
+  TRY(push(c, pl.d_f_o, fo.data(), no * sizeof(double), s));
+  // Psi_o (HY), b = 4 f omega psi (Rg), W = omega psi (Y)
+  double *Psi_o = c->HY, *R = c->Rg, *Wo = c->Y, *Po = c->P, *r64 = c->Y;
+  CU(launch_adjoint_rhs(c->X, nv, pl.d_idx, no, pl.d_f_o, dLdrho, c->mass, L, Psi_o, R, Wo, s),
+     "adjoint_rhs");
+  // J = Psi_o^T diag(omega) Psi_o;  eta (Eq. 9); along-Psi coefficients (Eq. 8)
+  double *J = c->small;
+  CU(launch_gram(Wo, no, Psi_o, no, L, J, c->partial, s), "gram(J)");
+  std::vector<double> Jh((size_t)no * no);
+  TRY(fetch(c, J, Jh.size() * sizeof(double), Jh.data(), s));
+  double sdf = 0.0, sdfI = 0.0;
+  for (int k = 0; k < no; ++k) {
+    sdf += dfde[pl.idx[k]];
+    sdfI += dfde[pl.idx[k]] * Jh[(size_t)k * no + k];
+  }
+  const double eta = sdf != 0.0 ? 2.0 * sdfI / sdf : 0.0;
+  std::vector<double> dco(np);
+  for (int cc = 0; cc < no; ++cc)
+    for (int k = pl.cs[cc]; k < pl.cs[cc + 1]; ++k) {
+      const int j = pl.ia[k];
+      dco[k] = dfde[pl.idx[cc]] * (-2.0 * Jh[(size_t)j * no + cc] + (j == cc ? eta : 0.0));
+    }
+  TRY(push(c, pl.d_dcoef, dco.data(), np * sizeof(double), s));
+  // g~ = P b (Eq. 10 removes the component along the degenerate set)
+  TRY(project<double>(c, pl, Psi_o, R, s));
+  std::vector<double> gn(no);
+  CU(launch_coldot(R, R, no, L, c->scal + kScCol, c->partial, s), "coldot");
+  TRY(fetch(c, c->scal + kScCol, no * sizeof(double), gn.data(), s));
+  for (auto &x : gn) x = std::sqrt(std::max(x, 0.0));
+  // iterative refinement around the inner MINRES (FP32 or FP64)
+  const double tad = adj_tolerance(c);
+  const size_t blk = (size_t)L * no;
+  CU(cudaMemsetAsync(Po, 0, blk * sizeof(double), s), "memset");
+  CU(cudaMemcpyAsync(r64, R, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  std::vector<double> rn(no), tol(no);
+  int total_iters = 0, outer = 0;
+  double relmax = 0.0;
+  invdft_status status = INVDFT_OK;
+  const bool mixed = c->o.prec == INVDFT_MIXED;
+  for (;; ++outer) {
+    CU(launch_coldot(r64, r64, no, L, c->scal + kScCol, c->partial, s), "coldot");
+    TRY(fetch(c, c->scal + kScCol, no * sizeof(double), rn.data(), s));
+    relmax = 0.0;
+    for (int k = 0; k < no; ++k) {
+      const double r = std::sqrt(std::max(rn[k], 0.0));
+      const double rel = gn[k] > 0 ? r / gn[k] : 0.0;
+      relmax = std::max(relmax, rel);
+      const double floor_tol = mixed ? 1e-6 : 1e-14;
+      tol[k] = rel > 0 ? std::max(floor_tol, std::min(0.5, 0.5 * tad / rel)) : 1.0;
+    }
+    if (relmax <= tad) break;
+    if (outer >= 12) {
+      status = INVDFT_ENOCONV;
+      c->err = "adjoint solve: refinement cap reached";
+      break;
+    }
+    int its = 0;
+    if (mixed) {
+      float *b32 = (float *)c->mr[8], *x32 = (float *)c->mr[7];
+      CU(launch_convert_f64_to_f32(r64, b32, (long long)blk, s), "convert");
+      TRY(minres_block<float>(c, pl, Psi_o, b32, x32, tol, c->o.max_minres_iters, &its, s));
+      CU((launch_add_convert<float, double>(x32, Po, (long long)blk, s)), "add");
+    } else {
+      double *b64 = (double *)c->mr[8], *x64 = (double *)c->mr[7];
+      CU(cudaMemcpyAsync(b64, r64, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+      TRY(minres_block<double>(c, pl, Psi_o, b64, x64, tol, c->o.max_minres_iters, &its, s));
+      CU((launch_add_convert<double, double>(x64, Po, (long long)blk, s)), "add");
+    }
+    total_iters += its;
+    TRY(project<double>(c, pl, Psi_o, Po, s));
+    // r = g~ - P (H~ - eps) P p
+    HxArgs<double> a;
+    a.X = Po;
+    a.Z = r64;
+    a.ncol = no;
+    a.alpha = -1.0;
+    a.shift_col = pl.d_eps_o;
+    a.W = R;
+    a.beta = 1.0;
+    CU(launch_hx(c->g, c->v, a, s), "hx(residual)");
+    TRY(project<double>(c, pl, Psi_o, r64, s));
+  }
+  // p~ = p_perp + Psi_k d (Eq. 8)
+  CU(launch_add_along(Psi_o, pl.d_cs, pl.d_ia, pl.d_dcoef, Po, no, L, s), "add_along");
+  if (p_full) {
+    CU(cudaMemsetAsync(p_full, 0, (size_t)L * nv * sizeof(double), s), "memset");
+    CU(launch_scatter_cols(Po, no, pl.d_idx, p_full, nv, L, s), "scatter");
+  }
+  if (stats) {
+    stats->adj_resid_max = relmax;
+    stats->eta = eta;
+    stats->minres_iters_max = std::max(stats->minres_iters_max, total_iters);
+    stats->refinements += outer;
+    stats->t_adjoint_ms += wall_ms() - t0;
+  }
+  if (plan_out) *plan_out = pl;
+  return status;
+}
+
+// ---------------------------------------------------------------- loss, gradient
+invdft_status loss_grad(Ctx *c, const double *rd, const double *w, double *grad,
+                        invdft_stats *stats, double *loss_out, cudaStream_t s) {
+  invdft_status fst = forward_solve(c, stats, s);
+  if (fst != INVDFT_OK && fst != INVDFT_ENOCONV) return fst;
+  double out3[3];
+  CU(launch_loss(c->rho, rd, w, c->mass, c->L, c->scal, c->dLdrho, c->partial, s), "loss");
+  TRY(fetch(c, c->scal, 3 * sizeof(double), out3, s));
+  c->loss = out3[0];
+  c->err_l2 = std::sqrt(std::max(out3[1], 0.0));
+  AdjPlan pl;
+  invdft_status ast = adjoint_solve(c, c->dLdrho, nullptr, stats, &pl, s);
+  if (ast != INVDFT_OK && ast != INVDFT_ENOCONV) return ast;
+  CU(launch_gradient(c->P, c->HY, pl.no, rd, c->o.tau_bc, c->L, grad, s), "gradient");
+  if (stats) {
+    stats->loss = c->loss;
+    stats->err_l2 = c->err_l2;
+    stats->n_elec = out3[2];
+  }
+  if (loss_out) *loss_out = c->loss;
+  return fst != INVDFT_OK ? fst : ast;
+}
+
+// loss only (line-search trial): forward + loss
+invdft_status loss_only(Ctx *c, const double *rd, const double *w, invdft_stats *stats,
+                        double *loss_out, double *err_out, cudaStream_t s) {
+  invdft_status fst = forward_solve(c, stats, s);
+  if (fst != INVDFT_OK && fst != INVDFT_ENOCONV) return fst;
+  double out3[3];
+  CU(launch_loss(c->rho, rd, w, c->mass, c->L, c->scal, nullptr, c->partial, s), "loss");
+  TRY(fetch(c, c->scal, 3 * sizeof(double), out3, s));
+  *loss_out = out3[0];
+  *err_out = std::sqrt(std::max(out3[1], 0.0));
+  if (stats) stats->n_elec = out3[2];
+  return INVDFT_OK;
+}
+
+invdft_status set_v(Ctx *c, const double *vxc, cudaStream_t s) {
+  CU(launch_lincomb(1.0, c->vfixed, 1.0, vxc, c->v, c->L, s), "set_v");
+  c->have_forward = false;
+  c->have_upper = false;
+  return INVDFT_OK;
+}
+
+double dot_host(Ctx *c, const double *x, const double *y, cudaStream_t s, invdft_status *st) {
+  double r = 0.0;
+  if (!cuda_ok(c, launch_dot(x, y, c->L, c->scal, c->partial, s), "dot")) {
+    *st = INVDFT_ECUDA;
+    return 0.0;
+  }
+  *st = fetch(c, c->scal, sizeof(double), &r, s);
+  return r;
+}
+
+// one L-BFGS iteration (Eq. 21) with backtracking; readings match the oracle
+invdft_status lbfgs_step(Ctx *c, const double *rd, const double *w, double *vxc,
+                         invdft_stats *stats, cudaStream_t s) {
+  const long long L = c->L;
+  invdft_status st = INVDFT_OK;
+  if (!c->have_grad) {
+    TRY(set_v(c, vxc, s));
+    double loss;
+    invdft_status r = loss_grad(c, rd, w, c->grad, stats, &loss, s);
+    if (r != INVDFT_OK && r != INVDFT_ENOCONV) return r;
+    c->have_grad = true;
+  }
+  // direction by the two-loop recursion
+  const int m = c->o.lbfgs_history;
+  const int k = c->hist_n;
+  double *d = c->dir;
+  if (k == 0) {
+    CU(launch_absmax(c->grad, L, c->scal, c->partial, s), "absmax");
+    double gmax;
+    TRY(fetch(c, c->scal, sizeof(double), &gmax, s));
+    CU(launch_lincomb(gmax > 0 ? -0.1 / gmax : 0.0, c->grad, 0.0, c->grad, d, L, s), "lincomb");
+  } else {
+    CU(cudaMemcpyAsync(d, c->grad, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    std::vector<double> alpha(k), rho(k);
+    auto slot = [&](int j) { return (c->hist_head - k + j + m) % m; };  // j = 0 oldest
+    for (int j = k - 1; j >= 0; --j) {
+      const double *Sj = c->Sh + (size_t)slot(j) * L, *Yj = c->Yh + (size_t)slot(j) * L;
+      rho[j] = 1.0 / dot_host(c, Yj, Sj, s, &st);
+      alpha[j] = rho[j] * dot_host(c, Sj, d, s, &st);
+      TRY(st);
+      CU(launch_axpby(-alpha[j], Yj, 1.0, d, L, s), "axpby");
+    }
+    const double *Sn = c->Sh + (size_t)slot(k - 1) * L, *Yn = c->Yh + (size_t)slot(k - 1) * L;
+    const double gamma = dot_host(c, Sn, Yn, s, &st) / dot_host(c, Yn, Yn, s, &st);
+    TRY(st);
+    CU(launch_axpby(0.0, d, gamma, d, L, s), "scale");
+    for (int j = 0; j < k; ++j) {
+      const double *Sj = c->Sh + (size_t)slot(j) * L, *Yj = c->Yh + (size_t)slot(j) * L;
+      const double beta = rho[j] * dot_host(c, Yj, d, s, &st);
+      TRY(st);
+      CU(launch_axpby(alpha[j] - beta, Sj, 1.0, d, L, s), "axpby");
+    }
+    CU(launch_axpby(0.0, d, -1.0, d, L, s), "negate");
+  }
+  const double slope = dot_host(c, c->grad, d, s, &st);
+  TRY(st);
+  double alpha = 1.0, L_try = 0.0, e_try = 0.0;
+  int trials = 0;
+  for (int t = 0; t < 10; ++t) {
+    CU(launch_lincomb(1.0, vxc, alpha, d, c->vtry, L, s), "trial");
+    TRY(set_v(c, c->vtry, s));
+    invdft_status r = loss_only(c, rd, w, stats, &L_try, &e_try, s);
+    if (r != INVDFT_OK && r != INVDFT_ENOCONV) return r;
+    ++trials;
+    if (L_try <= c->loss + 1e-4 * alpha * slope || t == 9) break;
+    alpha *= 0.5;
+  }
+  // gradient at the accepted point (forward data of the last trial are current)
+  {
+    double out3[3];
+    CU(launch_loss(c->rho, rd, w, c->mass, L, c->scal, c->dLdrho, c->partial, s), "loss");
+    TRY(fetch(c, c->scal, 3 * sizeof(double), out3, s));
+    c->loss = out3[0];
+    c->err_l2 = std::sqrt(std::max(out3[1], 0.0));
+    AdjPlan pl;
+    invdft_status ast = adjoint_solve(c, c->dLdrho, nullptr, stats, &pl, s);
+    if (ast != INVDFT_OK && ast != INVDFT_ENOCONV) return ast;
+    CU(launch_gradient(c->P, c->HY, pl.no, rd, c->o.tau_bc, L, c->grad_new, s), "gradient");
+    if (stats) {
+      stats->n_elec = out3[2];
+    }
+  }
+  // history: s = vtry - vxc, y = grad_new - grad
+  double *Ss = c->Sh + (size_t)c->hist_head * L, *Ys = c->Yh + (size_t)c->hist_head * L;
+  CU(launch_lincomb(1.0, c->vtry, -1.0, vxc, Ss, L, s), "s");
+  CU(launch_lincomb(1.0, c->grad_new, -1.0, c->grad, Ys, L, s), "y");
+  const double sy = dot_host(c, Ss, Ys, s, &st);
+  const double ss = dot_host(c, Ss, Ss, s, &st);
+  const double yy = dot_host(c, Ys, Ys, s, &st);
+  TRY(st);
+  if (sy > 1e-12 * std::sqrt(ss) * std::sqrt(yy)) {
+    c->hist_head = (c->hist_head + 1) % m;
+    c->hist_n = std::min(c->hist_n + 1, m);
+  }
+  CU(cudaMemcpyAsync(vxc, c->vtry, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  CU(cudaMemcpyAsync(c->grad, c->grad_new, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  if (stats) {
+    stats->loss = c->loss;
+    stats->err_l2 = c->err_l2;
+    stats->ls_trials = trials;
+  }
+  CU(cudaStreamSynchronize(s), "sync");
+  return INVDFT_OK;
+}
+
+}  // namespace invdft
+
+using namespace invdft;
+
+extern "C" {
+
+static bool ready(invdft_handle h, const char *who) {
+  if (!h->bound || !h->have_potential) {
+    h->err = std::string(who) + ": bind a workspace and set a potential first";
+    return false;
+  }
+  return true;
+}
+
+invdft_status invdft_forward_solve(invdft_handle h, double *psi, double *eps, double *occ,
+                                   double *rho, invdft_stats *stats, void *stream) {
+  if (!h) return INVDFT_EINVAL;
+  if (!ready(h, "forward_solve")) return INVDFT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  invdft_status st = forward_solve(h, stats, s);
+  if (st != INVDFT_OK && st != INVDFT_ENOCONV) return st;
+  const size_t n = h->nv;
+  if (psi) INV_CUDA(h, cudaMemcpyAsync(psi, h->X, (size_t)h->L * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (eps) INV_CUDA(h, cudaMemcpyAsync(eps, h->eps, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (occ) INV_CUDA(h, cudaMemcpyAsync(occ, h->occ, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (rho) INV_CUDA(h, cudaMemcpyAsync(rho, h->rho, (size_t)h->L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  INV_CUDA(h, cudaStreamSynchronize(s));
+  return st;
+}
+
+invdft_status invdft_adjoint_solve(invdft_handle h, const double *dLdrho, double *p,
+                                   invdft_stats *stats, void *stream) {
+  if (!h || !dLdrho) return INVDFT_EINVAL;
+  if (!ready(h, "adjoint_solve")) return INVDFT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  invdft_status st = adjoint_solve(h, dLdrho, p, stats, nullptr, s);
+  INV_CUDA(h, cudaStreamSynchronize(s));
+  return st;
+}
+
+invdft_status invdft_density_vjp(invdft_handle h, const double *dLdrho, double *grad_v,
+                                 invdft_stats *stats, void *stream) {
+  if (!h || !dLdrho || !grad_v) return INVDFT_EINVAL;
+  if (!ready(h, "density_vjp")) return INVDFT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  AdjPlan pl;
+  invdft_status st = adjoint_solve(h, dLdrho, nullptr, stats, &pl, s);
+  if (st != INVDFT_OK && st != INVDFT_ENOCONV) return st;
+  if (!cuda_ok(h, launch_gradient(h->P, h->HY, pl.no, nullptr, 0.0, h->L, grad_v, s), "gradient"))
+    return INVDFT_ECUDA;
+  INV_CUDA(h, cudaStreamSynchronize(s));
+  return st;
+}
+
+invdft_status invdft_loss_grad(invdft_handle h, const double *rd, const double *w, double *loss_out,
+                               double *grad, invdft_stats *stats, void *stream) {
+  if (!h || !rd || !w || !grad) return INVDFT_EINVAL;
+  if (!ready(h, "loss_grad")) return INVDFT_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  invdft_status st = loss_grad(h, rd, w, grad, stats, loss_out, s);
+  INV_CUDA(h, cudaStreamSynchronize(s));
+  return st;
+}
+
+invdft_status invdft_step(invdft_handle h, const double *rd, const double *w, double *vxc,
+                          invdft_stats *stats, void *stream) {
+  if (!h || !rd || !w || !vxc) return INVDFT_EINVAL;
+  if (!ready(h, "step")) return INVDFT_EINVAL;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return lbfgs_step(h, rd, w, vxc, stats, (cudaStream_t)stream);
+}
+
+}  // extern "C"

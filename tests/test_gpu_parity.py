@@ -1,0 +1,206 @@
+"""GPU-vs-oracle parity of every C-ABI call (needs a B300; marked gpu).
+
+Tolerances (stated per result):
+  H~X FP64: max over columns of ||Y_gpu - Y_ora|| / ||Y_ora|| <= 1e-10;
+  H~X FP32 storage / FP32 accumulation: same norm <= 2e-6 (u_32 times a small
+    growth factor of the 7 one-dimensional contractions and the assembly sum);
+  eigenvalues of occupied states: |d eps| <= 1e-6 Ha;
+  density: sqrt(sum_a m_a (rho_gpu - rho_ora)^2) <= 1e-6;
+  gradient: ||g_gpu - g_ora|| / ||g_ora|| <= 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import workloads as W  # noqa: E402
+from oracle import adjoint as oadj  # noqa: E402
+from oracle import chebyshev as ocheb  # noqa: E402
+from oracle import fe, inverse, ks, scf  # noqa: E402
+
+
+def _cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _problem(lo, hi, ncell, order, nstates, **kw):
+    import paper_2510_10529_b300 as P
+    return P.Problem(lo, hi, ncell, order, nstates, **kw)
+
+
+def _colrel(Yg, Yo):
+    return float(np.max(np.linalg.norm(Yg - Yo, axis=0) / np.linalg.norm(Yo, axis=0)))
+
+
+@pytest.fixture(scope="module")
+def cube8():
+    wl = W.cube8_q2_he()
+    mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
+    return wl, mesh, scf.target_density(mesh, wl)
+
+
+MESHES = [(-8.0, 8.0, 8, 2), (-6.0, 6.0, 6, 4), (-3.0, 3.0, 1, 4)]
+
+
+@pytest.mark.parametrize("geom", MESHES)
+@pytest.mark.parametrize("ncol", [1, 8, 13, 40])
+def test_apply_h_fp64_and_fp32_match_oracle(geom, ncol):
+    lo, hi, n, p = geom
+    mesh = fe.Mesh(lo, hi, n, p)
+    rng = np.random.default_rng(100 + ncol)
+    v = W.smeared_coulomb(mesh.coords(), np.array([[0.3, -0.1, 0.2]]), np.array([3.0]), 0.5)
+    v = v + 0.1 * rng.standard_normal(mesh.L)
+    X = rng.standard_normal((mesh.L, ncol))
+    Y_ora = mesh.apply_Htilde(v, X)
+    pb = _problem(lo, hi, n, p, nstates=min(ncol, 8))
+    pb.set_potential(_cuda(v))
+    Y64 = pb.apply_h(_cuda(X)).cpu().numpy()
+    assert _colrel(Y64, Y_ora) <= 1e-10
+    Y32 = pb.apply_h(_cuda(X, torch.float32)).double().cpu().numpy()
+    assert _colrel(Y32, Y_ora) <= 2e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 2e-6)])
+def test_apply_h_full_size_sampled_rows(dtype, tol):
+    """The 32^3-cell Q4 operator benchmark (2,048,383 unknowns, 64 columns) in the
+    launch configuration the benchmark times; 48 sampled rows against the
+    oracle's row-wise definition."""
+    wl = W.cube32_q4_hx()
+    mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=8)
+    xyz = pb.coords()
+    v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
+    pb.set_potential(_cuda(v))
+    X = _cuda(W.random_block(mesh.L, 64, wl.seed), dtype)
+    Y = pb.apply_h(X)
+    rng = np.random.default_rng(7)
+    rows = np.concatenate([rng.integers(0, mesh.L, 44), [0, mesh.L - 1, mesh.Ni - 1, mesh.L // 2]])
+    Xd = X.double()
+
+    def fetch(idx):
+        return Xd[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+
+    Yo = fe.htilde_rows(mesh, v[rows], rows, fetch)
+    Yg = Y[torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+    err = np.linalg.norm(Yg - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
+    assert err.max() <= tol
+
+
+def test_chebyshev_filter_matches_oracle(cube8):
+    wl, mesh, d = cube8
+    v = d["v_fixed"] + d["v_xc_ref"]
+    lam = np.linalg.eigvalsh(mesh.assemble_Htilde(v).toarray())
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((mesh.L, 8))
+    a, b, a0 = lam[10], lam[-1] * 1.01, lam[0]
+    Y_ora = ocheb.filter_apply(lambda Z: mesh.apply_Htilde(v, Z), X, 20, a, b, a0)
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=8)
+    pb.set_potential(_cuda(v))
+    Yg = pb.chebyshev_filter(_cuda(X), 20, a, b, a0).cpu().numpy()
+    assert _colrel(Yg, Y_ora) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_forward_solve_matches_oracle(cube8, prec):
+    wl, mesh, d = cube8
+    v = d["v_fixed"] + d["v_xc_ref"]
+    ora = ks.forward(mesh, v, wl.n_electrons, wl.nstates, wl.kT)
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=wl.nstates,
+                  n_electrons=wl.n_electrons, kT=wl.kT, prec=prec, eig_tol=1e-10,
+                  cheb_degree=wl.cheb_degree)
+    pb.set_potential(_cuda(d["v_fixed"]), _cuda(d["v_xc_ref"]))
+    out = pb.forward_solve()
+    occ = ora["f"] > 0
+    eps = out["eps"].cpu().numpy()
+    assert np.abs(eps[occ] - ora["eps"][occ]).max() <= 1e-6
+    rho = out["rho"].cpu().numpy()
+    m = mesh.mass()
+    assert math.sqrt(np.sum(m * (rho - ora["rho"]) ** 2)) <= 1e-6
+    assert abs(np.sum(m * rho) - wl.n_electrons) <= 1e-10
+    psi = out["psi"].cpu().numpy()
+    np.testing.assert_allclose(psi.T @ psi, np.eye(wl.nstates), atol=1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_loss_grad_matches_oracle(cube8, prec):
+    wl, mesh, d = cube8
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=wl.nstates,
+                  n_electrons=wl.n_electrons, kT=wl.kT, prec=prec, eig_tol=1e-10,
+                  adj_tol=1e-11, cheb_degree=wl.cheb_degree)
+    op = inverse.Problem(mesh=mesh, v_fixed=d["v_fixed"], rho_data=d["rho_data"],
+                         w=np.ones(mesh.L), n_electrons=wl.n_electrons, nstates=wl.nstates,
+                         kT=wl.kT)
+    v_xc = 0.3 * d["v_xc_ref"]
+    L_ora, e_ora, g_ora, _ = inverse.evaluate(op, v_xc)
+    pb.set_potential(_cuda(d["v_fixed"]), _cuda(v_xc))
+    loss, g, st = pb.loss_grad(_cuda(d["rho_data"]), _cuda(np.ones(mesh.L)))
+    g = g.cpu().numpy()
+    assert abs(loss - L_ora) <= 1e-8 * L_ora
+    assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_open_shell_degenerate_vjp_matches_oracle(prec):
+    """Partly filled exact triplet at kT > 0: the eta term and the matrix form of
+    the component along the degenerate set are exercised (Eq. 8-9)."""
+    mesh = fe.Mesh(-4.0, 4.0, 4, 2)
+    xyz = mesh.coords()
+    v = W.smeared_coulomb(xyz, np.zeros((1, 3)), np.array([3.0]), 0.5)
+    kT, Ne, nst = 0.02, 4.0, 8
+    rho_d = ks.forward(mesh, v + 0.05 * np.exp(-np.sum((xyz - 0.4) ** 2, 1)), Ne, nst, kT)["rho"]
+    fw = ks.forward(mesh, v, Ne, nst, kT)
+    G = oadj.loss_upstream(mesh, fw["rho"], rho_d, np.ones(mesh.L))
+    P_ora, _ = oadj.adjoint(mesh, v, fw["eps"], fw["psi"], fw["f"], fw["dfde"], G, solver="dense")
+    g_ora = oadj.gradient(fw["psi"], P_ora, rho_d, -1.0)
+    pb = _problem(-4.0, 4.0, 4, 2, nstates=nst, n_electrons=Ne, kT=kT, prec=prec,
+                  eig_tol=1e-11, adj_tol=1e-11, cheb_degree=16)
+    pb.set_potential(_cuda(v))
+    out = pb.forward_solve()
+    rho = out["rho"].cpu().numpy()
+    Gg = _cuda(oadj.loss_upstream(mesh, rho, rho_d, np.ones(mesh.L)))
+    g, st = pb.density_vjp(Gg)
+    g = g.cpu().numpy()
+    assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
+
+
+def test_lbfgs_steps_match_oracle(cube8):
+    wl, mesh, d = cube8
+    op = inverse.Problem(mesh=mesh, v_fixed=d["v_fixed"], rho_data=d["rho_data"],
+                         w=np.ones(mesh.L), n_electrons=wl.n_electrons, nstates=wl.nstates,
+                         kT=wl.kT)
+    st = inverse.State(v_xc=np.zeros(mesh.L))
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=wl.nstates,
+                  n_electrons=wl.n_electrons, kT=wl.kT, prec="fp64", eig_tol=1e-10,
+                  adj_tol=1e-11, cheb_degree=wl.cheb_degree)
+    pb.set_potential(_cuda(d["v_fixed"]))
+    v_xc = _cuda(np.zeros(mesh.L))
+    rd, w = _cuda(d["rho_data"]), _cuda(np.ones(mesh.L))
+    for _ in range(4):
+        st = inverse.step(op, st)
+        stats = pb.step(rd, w, v_xc)
+        vg = v_xc.cpu().numpy()
+        assert np.linalg.norm(vg - st.v_xc) <= 1e-6 * np.linalg.norm(st.v_xc)
+        assert abs(stats["loss"] - st.loss) <= 1e-6 * st.loss
+
+
+def test_autograd_backward_is_the_adjoint(cube8):
+    import paper_2510_10529_b300 as P
+    wl, mesh, d = cube8
+    pb = _problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=wl.nstates,
+                  n_electrons=wl.n_electrons, kT=wl.kT, prec="fp64", eig_tol=1e-10,
+                  adj_tol=1e-11, cheb_degree=wl.cheb_degree)
+    v_xc = _cuda(0.5 * d["v_xc_ref"]).requires_grad_(True)
+    m = _cuda(mesh.mass())
+    rd = _cuda(d["rho_data"])
+    rho = P.KohnShamDensity.apply(v_xc, pb, _cuda(d["v_fixed"]))
+    loss = torch.sum(m * (rd - rho) ** 2)
+    loss.backward()
+    op = inverse.Problem(mesh=mesh, v_fixed=d["v_fixed"], rho_data=d["rho_data"],
+                         w=np.ones(mesh.L), n_electrons=wl.n_electrons, nstates=wl.nstates,
+                         kT=wl.kT, tau_bc=-1.0)
+    _, _, g_ora, _ = inverse.evaluate(op, 0.5 * d["v_xc_ref"])
+    g = v_xc.grad.cpu().numpy()
+    assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
