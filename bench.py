@@ -1,0 +1,365 @@
+"""Benchmark: inverse-DFT iterations per second on one B300 (and replicas).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload cube32_q4_e100] [--prec mixed|fp64]
+
+A step is one full inverse iteration through the C ABI (invdft_step): the
+L-BFGS direction, a backtracking line search (one Kohn-Sham solve by
+Chebyshev-filtered subspace iteration per trial), the loss, the batched
+projected MINRES adjoint solves for every occupied orbital and the gradient
+reduction, with the paper's adaptive tolerances (c_eig = 1e2, c_ad = 1e5,
+tau_BC = 1e-6).  The default workload is the 100-electron, 32^3-cell Q4 case
+(2,048,383 unknowns, 60 states, 50 adjoint columns); the target density is
+generated at set-up by a Kohn-Sham solve at a known reference potential (the
+paper's molecular densities are not available).  Every orbital block is
+larger than L2 (0.98 GB in FP64), so no flush is needed between steps.
+
+The JSON line also carries the operator benchmark of the same mesh
+(H~X on 64 vectors, nominal 2 (p+1)^6 N_v n_cells flops), the roofline of the
+dominant kernel (H~X, timed with CUDA events inside the timed steps), the
+oracle as a CPU baseline, an end-to-end figure through host buffers and the
+SM clocks sampled during the timed region.
+
+Multi-GPU: the path runs as independent replicas (one problem per rank, no
+collective in the data path); value = steps of all ranks / max rank time.
+--impl reference times the FP64 CPU oracle on bounded samples of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
+
+# H~X column-applications per inverse iteration on each workload, as counted by
+# the GPU path (line-search solves, Chebyshev passes, MINRES iterations); the
+# reference arm uses these fixed counts so that it never touches the GPU.
+COL_APPLIES_PER_STEP = {"cube32_q4_e100": 60 * 31 * 3 + 50 * 300,
+                        "cube24_q4_e20": 16 * 31 * 3 + 10 * 200,
+                        "cube8_q2_he": 8 * 21 * 3 + 100, "cube32_q4_hx": 64}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube32_q4_e100", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-hx", action="store_true", help="skip the operator benchmark")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons every 200 ms (read only)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ problem set-up
+
+def build_problem(wl, prec, device):
+    import torch
+
+    import paper_2510_10529_b300 as P
+    pb = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, wl.nstates, n_electrons=wl.n_electrons,
+                   kT=wl.kT, prec=prec, cheb_degree=wl.cheb_degree, seed=wl.seed + 1,
+                   device=device)
+    xyz = pb.coords()
+    f = W.model_fields(wl, xyz)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=device).contiguous()
+    v_fixed, v_ref = t(f["v_fixed"]), t(f["v_xc_ref"])
+    # target density: a tight Kohn-Sham solve at the reference potential
+    gen = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, wl.nstates, n_electrons=wl.n_electrons,
+                    kT=wl.kT, prec="mixed", cheb_degree=wl.cheb_degree, eig_tol=1e-9,
+                    seed=wl.seed + 2, device=device)
+    gen.set_potential(v_fixed, v_ref)
+    rho_data = gen.forward_solve()["rho"].clone()
+    gen.close()
+    del gen
+    torch.cuda.empty_cache()
+    pb.set_potential(v_fixed, None)
+    return pb, dict(v_fixed=v_fixed, v_ref=v_ref, rho_data=rho_data,
+                    w=torch.ones(pb.L, dtype=torch.float64, device=device))
+
+
+def hx_benchmark(device, reps32=20, reps64=3):
+    """H~X on the 32^3-cell Q4 operator benchmark (64 unit-norm random vectors)."""
+    import torch
+
+    import paper_2510_10529_b300 as P
+    wl = W.cube32_q4_hx()
+    pb = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=8, device=device)
+    xyz = pb.coords()
+    v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
+    pb.set_potential(torch.as_tensor(v, dtype=torch.float64, device=device))
+    X64 = torch.as_tensor(W.random_block(pb.L, 64, wl.seed), device=device)
+    out = {}
+    ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
+    flops = 2.0 * ne * ne * 64 * cells
+    for name, X, reps in (("mixed", X64.float(), reps32), ("fp64", X64, reps64)):
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            P.invdft_apply_h(pb.h, X, Y)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            P.invdft_apply_h(pb.h, X, Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        byt = (2 * 64 * X.element_size() + 8) * pb.L
+        out[name] = {"ms": ms, "tflops_nominal": flops / ms / 1e9, "gbs": byt / ms / 1e6}
+    pb.close()
+    return {"workload": "cube32_q4_hx", "ncol": 64, "nominal_flops": flops, **out}
+
+
+# ------------------------------------------------------------------ oracle baseline
+
+def oracle_baseline(wl, col_applies_per_step: float, budget_s: float = 12.0):
+    """Time the oracle's H~X (numpy FP64 cell loop) on the full mesh with a few
+    columns, and scale to the column-applications of one GPU step."""
+    from oracle import fe
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
+    except Exception:
+        cores = 1
+    mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
+    ncol = 2
+    X = W.random_block(mesh.L, ncol, wl.seed)
+    v = np.zeros(mesh.L)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        mesh.apply_Htilde(v, X)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 8:
+            break
+    per_col = (time.perf_counter() - t0) / (reps * ncol)
+    step_s = per_col * col_applies_per_step
+    return {"value": 1.0 / step_s, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle H~X (numpy FP64 cell loop, {wl.name} mesh, {ncol} columns, "
+                       f"{reps} applications, {per_col:.3f} s per column) x "
+                       f"{col_applies_per_step:.0f} column-applications per step; a lower "
+                       "bound on the oracle's time per iteration (its Gram, eigensolver and "
+                       "MINRES vector work are not counted)")}
+
+
+# ------------------------------------------------------------------ arms
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2510_10529_b300 as P
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    wl = W.WORKLOADS[args.workload]()
+    pb, d = build_problem(wl, args.prec, device)
+    v_xc = torch.zeros(pb.L, dtype=torch.float64, device=device)
+    rd, w = d["rho_data"], d["w"]
+    for _ in range(args.warmup):
+        pb.step(rd, w, v_xc)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    pb.profile_hx(True)
+    launches0 = P.invdft_kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(pb.step(rd, w, v_xc))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = P.invdft_kernel_launches() - launches0
+    prof = pb.profile_hx(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t_max = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    ms_max = float(t_max.item())
+    value = world / (ms_max / 1e3)
+
+    # end to end through host buffers: v_xc pinned on the host, copied in and
+    # out every step, plus the loss read back
+    v_host = v_xc.cpu().pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        v_dev = v_host.to(device, non_blocking=True)
+        pb.step(rd, w, v_dev)
+        v_host.copy_(v_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": pb.L * 8,
+           "d2h_bytes_per_step": pb.L * 8 + 8}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    hx = None if args.no_hx else hx_benchmark(device)
+    pk = peaks()
+    k32 = prof["fp32"] if prof["fp32"]["launches"] > 0 else prof["fp64"]
+    achieved = k32["bytes"] / (k32["ms"] * 1e6) if k32["ms"] > 0 else None
+    peak_gbs = pk["hbm_gbs"] if pk else 6400.0
+    ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
+    col_applies = (prof["fp32"]["flops"] + prof["fp64"]["flops"]) / (2.0 * ne * ne * cells)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": (achieved / peak_gbs) if achieved else None, "traffic": None,
+            "kernel": "H~X (FP32 storage) inside the timed steps",
+            "launches": int(k32["launches"]), "avg_launch_ms": k32["ms"] / max(1, k32["launches"]),
+            "peak_source": "measured" if pk else "fallback",
+            "algorithmic_bytes_per_launch": k32["bytes"] / max(1, k32["launches"])}
+    cpu = None
+    if not args.no_cpu:
+        cpu = oracle_baseline(wl, col_applies / args.steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "cells": f"{wl.ncell}^3", "order": wl.order,
+                   "unknowns": pb.L, "nstates": wl.nstates, "n_electrons": wl.n_electrons,
+                   "prec": args.prec, "cheb_degree": wl.cheb_degree,
+                   "l2": "inputs larger than L2 (orbital blocks 0.98 GB FP64), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk, "hx": hx,
+        "step_stats": {"loss_last": stats[-1]["loss"], "err_l2_last": stats[-1]["err_l2"],
+                       "cheb_passes": [s["cheb_passes"] for s in stats],
+                       "minres_iters": [s["minres_iters_max"] for s in stats],
+                       "ls_trials": [s["ls_trials"] for s in stats],
+                       "col_applies_per_step": col_applies / args.steps,
+                       "hx_ms_share": (prof["fp32"]["ms"] + prof["fp64"]["ms"])
+                       / (ms_max * args.steps),
+                       "hx_fp64_ms_per_step": prof["fp64"]["ms"] / args.steps,
+                       "hx_fp32_ms_per_step": prof["fp32"]["ms"] / args.steps},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl = W.WORKLOADS[args.workload]()
+    per_step = COL_APPLIES_PER_STEP[wl.name]
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(oracle_baseline(wl, per_step, budget_s=4.0))
+    vals = vals[args.warmup:]
+    v = statistics.median([x["value"] for x in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells": f"{wl.ncell}^3", "order": wl.order,
+                       "unknowns": wl.n_interior, "nstates": wl.nstates,
+                       "n_electrons": wl.n_electrons, "parallelism": "cpu"},
+            "cpu_baseline": {**vals[-1], "value": v},
+            "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,19 @@ invdft_status invdft_loss_grad(invdft_handle h, const double *rho_data_dev, cons
 invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const double *w_dev,
                           double *v_xc_dev, invdft_stats *stats, void *stream);
 
+/* Instrumentation for benchmarks (no counterpart in the paper).
+ * invdft_profile_hx: while enabled, every H~X launch of this handle is
+ * bracketed by CUDA events on its stream.  Each call first drains pending
+ * events (synchronising on them) and, if out8 != NULL, writes the totals
+ * since the last enable: out8[0..3] = FP64 {device ms, algorithmic bytes
+ * (X and v read, Z written, plus W/E when present), nominal dense-cell
+ * flops 2 (p+1)^6 ncol ncell^3, launches}, out8[4..7] the same for FP32.
+ * enable = 1 resets the totals and turns timing on; 0 turns it off.
+ * invdft_kernel_launches: process-wide count of kernels launched by this
+ * library since it was loaded.                                              */
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out8);
+invdft_status invdft_kernel_launches(unsigned long long *count);
+
 /* Forget the L-BFGS history and the warm-start orbitals.                   */
 invdft_status invdft_reset(invdft_handle h);
 

@@ -141,6 +141,20 @@ def invdft_reset(h):
     return lib.invdft_reset(h)
 
 
+def invdft_profile_hx(h, enable: bool):
+    out = np.zeros(8)
+    _ok("invdft_profile_hx", lib.invdft_profile_hx(h, int(enable), out.ctypes.data_as(C.c_void_p)),
+        h, False)
+    keys = ("ms", "bytes", "flops", "launches")
+    return {"fp64": dict(zip(keys, out[:4])), "fp32": dict(zip(keys, out[4:]))}
+
+
+def invdft_kernel_launches() -> int:
+    n = C.c_ulonglong()
+    lib.invdft_kernel_launches(C.byref(n))
+    return n.value
+
+
 # ----------------------------------------------------------- owning wrapper
 
 class Problem:
@@ -238,6 +252,9 @@ class Problem:
 
     def reset(self):
         invdft_reset(self.h)
+
+    def profile_hx(self, enable: bool):
+        return invdft_profile_hx(self.h, enable)
 
 
 class KohnShamDensity(torch.autograd.Function):

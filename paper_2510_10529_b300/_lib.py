@@ -78,6 +78,8 @@ def _load():
         "invdft_loss_grad": [H, P, P, C.POINTER(C.c_double), P, C.POINTER(Stats), P],
         "invdft_step": [H, P, P, P, C.POINTER(Stats), P],
         "invdft_reset": [H],
+        "invdft_profile_hx": [H, C.c_int, P],
+        "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

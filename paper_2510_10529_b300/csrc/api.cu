@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.h"
@@ -15,6 +16,9 @@ using namespace invdft;
 namespace invdft {
 
 static thread_local std::string g_create_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return true;
@@ -162,6 +166,7 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
 invdft_status invdft_destroy(invdft_handle h) {
   if (!h) return INVDFT_EINVAL;
   if (h->hbuf) cudaFreeHost(h->hbuf);
+  for (auto e : h->prof.ev) cudaEventDestroy(e);
   delete h;
   return INVDFT_OK;
 }
@@ -200,6 +205,7 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   INV_CUDA(h, cudaMemcpyAsync(m1, tabs.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(kA, tabs.data() + N, N * sizeof(double), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(kB, tabs.data() + 2 * N, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  ::invdft::count_launch();
   init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag);
   INV_LAUNCH(h, "init_fields");
   INV_CUDA(h, cudaMemsetAsync(h->v, 0, h->L * sizeof(double), s));
@@ -251,6 +257,7 @@ invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed, const
   }
   cudaStream_t s = (cudaStream_t)stream;
   INV_CUDA(h, cudaMemcpyAsync(h->vfixed, v_fixed, h->L * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ::invdft::count_launch();
   add_fields<<<grid_for(h->L), 256, 0, s>>>(v_fixed, v_xc, h->v, h->L);
   INV_LAUNCH(h, "add_fields");
   h->have_potential = true;
@@ -277,13 +284,13 @@ invdft_status invdft_apply_h(invdft_handle h, const void *X, void *Y, int ncol,
     a.X = (const double *)X;
     a.Z = (double *)Y;
     a.ncol = ncol;
-    e = launch_hx(h->g, h->v, a, s);
+    e = hx_op(h, a, s);
   } else {
     HxArgs<float> a;
     a.X = (const float *)X;
     a.Z = (float *)Y;
     a.ncol = ncol;
-    e = launch_hx(h->g, h->v, a, s);
+    e = hx_op(h, a, s);
   }
   if (!cuda_ok(h, e, "apply_h")) return INVDFT_ECUDA;
   return INVDFT_OK;
@@ -310,6 +317,34 @@ invdft_status invdft_reset(invdft_handle h) {
   h->have_grad = false;
   h->have_upper = false;
   h->hist_n = h->hist_head = 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out8) {
+  if (!h) return INVDFT_EINVAL;
+  HxProf &p = h->prof;
+  if (!cuda_ok(h, prof_flush(h), "profile flush")) return INVDFT_ECUDA;
+  if (out8) {
+    for (int t = 0; t < 2; ++t) {
+      out8[4 * t + 0] = p.ms[t];
+      out8[4 * t + 1] = p.bytes_sum[t];
+      out8[4 * t + 2] = p.flops_sum[t];
+      out8[4 * t + 3] = (double)p.n[t];
+    }
+  }
+  if (enable) {
+    for (int t = 0; t < 2; ++t) {
+      p.ms[t] = p.bytes_sum[t] = p.flops_sum[t] = 0.0;
+      p.n[t] = 0;
+    }
+  }
+  p.on = enable != 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_kernel_launches(unsigned long long *count) {
+  if (!count) return INVDFT_EINVAL;
+  *count = g_launches.load(std::memory_order_relaxed);
   return INVDFT_OK;
 }
 

@@ -72,9 +72,11 @@ cudaError_t gram_t(const TA *A, int n1, const TA *B, int n2, long long L, double
                    double *partial, cudaStream_t s) {
   if (n1 < 1 || n2 < 1 || n1 > kMaxGram || n2 > kMaxGram) return cudaErrorInvalidValue;
   dim3 grid(kGramBlocks, (n1 + kTile - 1) / kTile, (n2 + kTile - 1) / kTile);
+  ::invdft::count_launch();
   gram_partial<TA><<<grid, 256, 0, s>>>(A, n1, B, n2, L, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
   sum_partials<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, n1, n2, G);
   return cudaGetLastError();
 }
@@ -144,9 +146,11 @@ template <typename TA>
 cudaError_t coldot_t(const TA *A, const TA *B, int ncol, long long L, double *d, double *partial,
                      cudaStream_t s) {
   if (ncol < 1 || ncol > kMaxCols) return cudaErrorInvalidValue;
+  ::invdft::count_launch();
   coldot_partial<TA><<<kGramBlocks, 256, 0, s>>>(A, B, ncol, L, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
   sum_col_partials<<<(ncol + 127) / 128, 128, 0, s>>>(partial, kGramBlocks, ncol, d);
   return cudaGetLastError();
 }
@@ -201,6 +205,7 @@ cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, lo
   cudaError_t e = cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
   rotate_kernel<<<148 * 4, 256, smem, s>>>(Xi, n1, Cm, n2, L, Xo);
   return cudaGetLastError();
 }
@@ -213,14 +218,17 @@ cudaError_t launch_coldot_f32(const float *A, const float *B, int ncol, long lon
   return coldot_t<float>(A, B, ncol, L, d, partial, s);
 }
 cudaError_t launch_convert_f64_to_f32(const double *x, float *y, long long n, cudaStream_t s) {
+  ::invdft::count_launch();
   conv_d2f<<<grid_for(n), 256, 0, s>>>(x, y, n);
   return cudaGetLastError();
 }
 cudaError_t launch_convert_f32_to_f64(const float *x, double *y, long long n, cudaStream_t s) {
+  ::invdft::count_launch();
   conv_f2d<<<grid_for(n), 256, 0, s>>>(x, y, n);
   return cudaGetLastError();
 }
 cudaError_t launch_fill_random(double *X, long long n, unsigned long long seed, cudaStream_t s) {
+  ::invdft::count_launch();
   fill_normal<<<grid_for(n), 256, 0, s>>>(X, n, seed);
   return cudaGetLastError();
 }

@@ -255,12 +255,14 @@ cudaError_t launch_rr_small(const double *S, const double *H, int n, double *the
   cudaError_t e = cudaFuncSetAttribute(rr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
   rr_small<<<1, 1024, smem, s>>>(S, H, n, theta, C, status, work, work + (size_t)n * n, 60);
   return cudaGetLastError();
 }
 
 cudaError_t launch_occupations(const double *eps, int n, double ne, double kT, double *f,
                                double *dfde, double *mu, int *status, cudaStream_t s) {
+  ::invdft::count_launch();
   occupations_kernel<<<1, 32, 0, s>>>(eps, n, ne, kT, f, dfde, mu, status);
   return cudaGetLastError();
 }

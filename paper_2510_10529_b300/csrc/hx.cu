@@ -167,6 +167,7 @@ cudaError_t run_cells(const Geom &g, const T *X, T *Z, int ncol, double scale, c
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ncell * g.ncell * g.ncell, (ncol + C - 1) / C);
+  ::invdft::count_launch();
   k<<<grid, 256, smem, s>>>(X, Z, ncol, g, scale);
   return cudaGetLastError();
 }
@@ -183,6 +184,7 @@ cudaError_t launch_hx_t(const Geom &g, const double *v, const HxArgs<T> &a, cuda
   if (a.ncol < 1 || a.ncol > kMaxCols) return cudaErrorInvalidValue;
   const long long n = g.L * a.ncol;
   int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
+  ::invdft::count_launch();
   hx_nodal<T><<<blocks, 256, 0, s>>>(a.X, a.Z, v, g.L, a.ncol, a.alpha, a.shift, a.shift_col, a.W,
                                      a.beta, a.E, a.escale);
   cudaError_t e = cudaGetLastError();
@@ -201,5 +203,69 @@ cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<double> &a, c
 cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cudaStream_t s) {
   return launch_hx_t<float>(g, v, a, s);
 }
+
+}  // namespace invdft
+
+namespace invdft {
+namespace {
+
+template <typename T>
+cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
+  HxProf &p = c->prof;
+  if (!p.on) return launch_hx(c->g, c->v, a, s);
+  const int slots = 1024;
+  if (p.ev.empty()) {
+    p.ev.resize(2 * slots);
+    p.kind.resize(slots);
+    p.bytes.resize(slots);
+    p.flops.resize(slots);
+    for (auto &e : p.ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) return r;
+    }
+  }
+  if (p.used == slots) {
+    cudaError_t r = prof_flush(c);
+    if (r != cudaSuccess) return r;
+  }
+  const int k = p.used++;
+  const double L = (double)c->L, n = a.ncol, sz = sizeof(T);
+  double bytes = (2.0 * n * sz + 8.0) * L;            // X read, Z written, v read
+  if (a.W) bytes += n * sz * L;
+  if (a.E) bytes += n * 4.0 * L;
+  const double ne = (double)c->g.q * c->g.q * c->g.q;
+  const double cells = (double)c->g.ncell * c->g.ncell * c->g.ncell;
+  p.kind[k] = sizeof(T) == 8 ? 0 : 1;
+  p.bytes[k] = bytes;
+  p.flops[k] = 2.0 * ne * ne * n * cells;
+  cudaEventRecord(p.ev[2 * k], s);
+  cudaError_t r = launch_hx(c->g, c->v, a, s);
+  cudaEventRecord(p.ev[2 * k + 1], s);
+  return r;
+}
+
+}  // namespace
+
+cudaError_t prof_flush(Ctx *c) {
+  HxProf &p = c->prof;
+  if (p.used == 0) return cudaSuccess;
+  cudaError_t r = cudaEventSynchronize(p.ev[2 * (p.used - 1) + 1]);
+  if (r != cudaSuccess) return r;
+  for (int k = 0; k < p.used; ++k) {
+    float ms = 0.f;
+    r = cudaEventElapsedTime(&ms, p.ev[2 * k], p.ev[2 * k + 1]);
+    if (r != cudaSuccess) return r;
+    const int t = p.kind[k];
+    p.ms[t] += ms;
+    p.bytes_sum[t] += p.bytes[k];
+    p.flops_sum[t] += p.flops[k];
+    p.n[t] += 1;
+  }
+  p.used = 0;
+  return cudaSuccess;
+}
+
+cudaError_t hx_op(Ctx *c, const HxArgs<double> &a, cudaStream_t s) { return hx_op_t(c, a, s); }
+cudaError_t hx_op(Ctx *c, const HxArgs<float> &a, cudaStream_t s) { return hx_op_t(c, a, s); }
 
 }  // namespace invdft

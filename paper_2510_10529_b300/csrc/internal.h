@@ -54,7 +54,21 @@ struct Arena {
   }
 };
 
+// CUDA-event timing of every H~X launch while enabled (benchmark evidence):
+// per precision (0 = FP64, 1 = FP32) the summed device time, algorithmic
+// bytes, nominal dense-cell flops and launch count.
+struct HxProf {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;     // 2 per slot
+  std::vector<int> kind;
+  std::vector<double> bytes, flops;
+  int used = 0;
+  double ms[2] = {0, 0}, bytes_sum[2] = {0, 0}, flops_sum[2] = {0, 0};
+  long long n[2] = {0, 0};
+};
+
 struct Ctx {
+  HxProf prof;
   invdft_mesh_desc mesh{};
   invdft_opts o{};
   Tables tab;
@@ -112,6 +126,8 @@ namespace invdft {
 
 // ------------------------------------------------------------ error helpers
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what);
+// process-wide count of kernels this library has launched (benchmark evidence)
+void count_launch();
 #define INV_CUDA(c, call)                                   \
   do {                                                      \
     if (!::invdft::cuda_ok((c), (call), #call)) return INVDFT_ECUDA; \
@@ -140,6 +156,10 @@ struct HxArgs {
 };
 cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<double> &a, cudaStream_t s);
 cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cudaStream_t s);
+// launch_hx on the handle's operator, timed with CUDA events when profiling is on
+cudaError_t hx_op(Ctx *c, const HxArgs<double> &a, cudaStream_t s);
+cudaError_t hx_op(Ctx *c, const HxArgs<float> &a, cudaStream_t s);
+cudaError_t prof_flush(Ctx *c);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).

@@ -325,6 +325,7 @@ __global__ void add_convert_kernel(const TI *__restrict__ d, TO *__restrict__ p,
 
 cudaError_t launch_density(const double *X, int n, const double *occ, const double *mass,
                            long long L, double *rho, cudaStream_t s) {
+  ::invdft::count_launch();
   density_kernel<<<grid_for(L), 256, 0, s>>>(X, n, occ, mass, L, rho);
   return cudaGetLastError();
 }
@@ -332,7 +333,9 @@ cudaError_t launch_density(const double *X, int n, const double *occ, const doub
 cudaError_t launch_loss(const double *rho, const double *rd, const double *w, const double *mass,
                         long long L, double *out3, double *dLdrho, double *partial,
                         cudaStream_t s) {
+  ::invdft::count_launch();
   loss_partial<<<kGramBlocks, 256, 0, s>>>(rho, rd, w, mass, L, partial, dLdrho);
+  ::invdft::count_launch();
   sum3<<<1, 32, 0, s>>>(partial, kGramBlocks, out3);
   return cudaGetLastError();
 }
@@ -340,6 +343,7 @@ cudaError_t launch_loss(const double *rho, const double *rd, const double *w, co
 cudaError_t launch_adjoint_rhs(const double *X, int nv, const int *idx, int no, const double *f_o,
                                const double *dLdrho, const double *mass, long long L,
                                double *Psi_o, double *R, double *Wo, cudaStream_t s) {
+  ::invdft::count_launch();
   adjoint_rhs_kernel<<<grid_for(L * no), 256, 0, s>>>(X, nv, idx, no, f_o, dLdrho, mass, L, Psi_o,
                                                       R, Wo);
   return cudaGetLastError();
@@ -351,7 +355,9 @@ cudaError_t launch_pairdot(const TA *A, int lda, const int *ia, const TB *B, int
                            cudaStream_t s) {
   if (npairs < 1 || npairs > kMaxDense * kMaxGroup) return cudaErrorInvalidValue;
   dim3 grid(kGramBlocks, (npairs + 255) / 256);
+  ::invdft::count_launch();
   pairdot_partial<TA, TB><<<grid, 256, 0, s>>>(A, lda, ia, B, ldb, ib, npairs, L, partial);
+  ::invdft::count_launch();
   pair_sum<<<(npairs + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, npairs, coef);
   return cudaGetLastError();
 }
@@ -365,6 +371,7 @@ template cudaError_t launch_pairdot<double, float>(const double *, int, const in
 template <typename T>
 cudaError_t launch_project_apply(const double *Psi, int ldp, const int *col_start, const int *ia,
                                  const double *coef, T *X, int ncol, long long L, cudaStream_t s) {
+  ::invdft::count_launch();
   project_apply_kernel<T><<<grid_for(L * ncol), 256, 0, s>>>(Psi, ldp, col_start, ia, coef, -1.0,
                                                              X, ncol, L);
   return cudaGetLastError();
@@ -378,6 +385,7 @@ template cudaError_t launch_project_apply<float>(const double *, int, const int 
 
 cudaError_t launch_add_along(const double *Psi_o, const int *col_start, const int *ia,
                              const double *dcoef, double *P, int n, long long L, cudaStream_t s) {
+  ::invdft::count_launch();
   project_apply_kernel<double><<<grid_for(L * n), 256, 0, s>>>(Psi_o, n, col_start, ia, dcoef, 1.0,
                                                                P, n, L);
   return cudaGetLastError();
@@ -385,44 +393,54 @@ cudaError_t launch_add_along(const double *Psi_o, const int *col_start, const in
 
 cudaError_t launch_gradient(const double *P, const double *Psi, int ncol, const double *rd,
                             double tau, long long L, double *grad, cudaStream_t s) {
+  ::invdft::count_launch();
   gradient_kernel<<<grid_for(L), 256, 0, s>>>(P, Psi, ncol, rd, tau, L, grad);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot(const double *x, const double *y, long long n, double *out, double *partial,
                        cudaStream_t s) {
+  ::invdft::count_launch();
   dot_partial<<<kGramBlocks, 256, 0, s>>>(x, y, n, partial);
+  ::invdft::count_launch();
   reduce_partials<<<1, 32, 0, s>>>(partial, kGramBlocks, 0, out);
   return cudaGetLastError();
 }
 cudaError_t launch_absmax(const double *x, long long n, double *out, double *partial,
                           cudaStream_t s) {
+  ::invdft::count_launch();
   absmax_partial<<<kGramBlocks, 256, 0, s>>>(x, n, partial);
+  ::invdft::count_launch();
   reduce_partials<<<1, 32, 0, s>>>(partial, kGramBlocks, 1, out);
   return cudaGetLastError();
 }
 cudaError_t launch_axpby(double a, const double *x, double b, double *y, long long n,
                          cudaStream_t s) {
+  ::invdft::count_launch();
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(a, x, b, y, n);
   return cudaGetLastError();
 }
 cudaError_t launch_lincomb(double a, const double *x, double b, const double *y, double *out,
                            long long n, cudaStream_t s) {
+  ::invdft::count_launch();
   lincomb_kernel<<<grid_for(n), 256, 0, s>>>(a, x, b, y, out, n);
   return cudaGetLastError();
 }
 cudaError_t launch_residual_block(const double *HX, const double *X, const double *theta, int n,
                                   long long L, double *E64, float *E32, cudaStream_t s) {
+  ::invdft::count_launch();
   residual_block_kernel<<<grid_for(L * n), 256, 0, s>>>(HX, X, theta, n, L, E64, E32);
   return cudaGetLastError();
 }
 cudaError_t launch_cheb_combine(const double *X, const double *pm, const float *D, int n,
                                 long long L, double *Y, cudaStream_t s) {
+  ::invdft::count_launch();
   cheb_combine_kernel<<<grid_for(L * n), 256, 0, s>>>(X, pm, D, n, L, Y);
   return cudaGetLastError();
 }
 cudaError_t launch_scale_f32(const float *E, const double *, double alpha, int n, long long L,
                              float *D, cudaStream_t s) {
+  ::invdft::count_launch();
   scale_f32_kernel<<<grid_for(L * n), 256, 0, s>>>(E, alpha, n, L, D);
   return cudaGetLastError();
 }
@@ -431,6 +449,7 @@ template <typename T>
 cudaError_t launch_mr_lanczos(const T *p, const T *q, const T *qprev, const double *alpha,
                               const double *beta, const double *prec, int n, long long L, T *qhat,
                               T *zhat, cudaStream_t s) {
+  ::invdft::count_launch();
   mr_lanczos_kernel<T><<<grid_for(L * n), 256, 0, s>>>(p, q, qprev, alpha, beta, prec, n, L, qhat,
                                                        zhat);
   return cudaGetLastError();
@@ -438,32 +457,38 @@ cudaError_t launch_mr_lanczos(const T *p, const T *q, const T *qprev, const doub
 template <typename T>
 cudaError_t launch_mr_update(T *z, const T *zhat, T *qn, const T *qhat, T *wpp, const T *wp, T *x,
                              const double *st, int n, long long L, cudaStream_t s) {
+  ::invdft::count_launch();
   mr_update_kernel<T><<<grid_for(L * n), 256, 0, s>>>(z, zhat, qn, qhat, wpp, wp, x, st, n, L);
   return cudaGetLastError();
 }
 cudaError_t launch_mr_givens(int n, double *st, cudaStream_t s) {
+  ::invdft::count_launch();
   mr_givens_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, st);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mr_init(const T *b, const T *zb, const double *beta1, int n, long long L, T *q,
                            T *z, cudaStream_t s) {
+  ::invdft::count_launch();
   mr_init_kernel<T><<<grid_for(L * n), 256, 0, s>>>(b, zb, beta1, n, L, q, z);
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_prec_apply(const T *r, const double *prec, int n, long long L, T *z,
                               cudaStream_t s) {
+  ::invdft::count_launch();
   prec_apply_kernel<T><<<grid_for(L * n), 256, 0, s>>>(r, prec, n, L, z);
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_cols(const double *Po, int no, const int *idx, double *P, int nv,
                                 long long L, cudaStream_t s) {
+  ::invdft::count_launch();
   scatter_cols_kernel<<<grid_for(L * no), 256, 0, s>>>(Po, no, idx, P, nv, L);
   return cudaGetLastError();
 }
 template <typename TI, typename TO>
 cudaError_t launch_add_convert(const TI *d, TO *p, long long n, cudaStream_t s) {
+  ::invdft::count_launch();
   add_convert_kernel<TI, TO><<<grid_for(n), 256, 0, s>>>(d, p, n);
   return cudaGetLastError();
 }

@@ -113,7 +113,7 @@ invdft_status upper_bound(Ctx *c, cudaStream_t s, double *out) {
     a.ncol = 1;
     a.W = v0;
     a.beta = -beta;                  // f = H v - beta v0
-    CU(launch_hx(c->g, c->v, a, s), "hx(lanczos)");
+    CU(hx_op(c, a, s), "hx(lanczos)");
     CU(launch_dot(f, v, L, sc, c->partial, s), "dot");
     double alpha;
     TRY(fetch(c, sc, sizeof(double), &alpha, s));
@@ -163,7 +163,7 @@ invdft_status apply_h_f64(Ctx *c, const double *X, double *Z, int n, cudaStream_
   a.X = X;
   a.Z = Z;
   a.ncol = n;
-  CU(launch_hx(c->g, c->v, a, s), "hx");
+  CU(hx_op(c, a, s), "hx");
   return INVDFT_OK;
 }
 
@@ -211,7 +211,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
         h.shift = cc;
         h.W = (const double *)prev;
         h.beta = beta;
-        err = launch_hx(c->g, c->v, h, s);
+        err = hx_op(c, h, s);
       } else {
         HxArgs<float> h;
         h.X = (const float *)cur;
@@ -221,7 +221,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
         h.shift = cc;
         h.W = (const float *)prev;
         h.beta = beta;
-        err = launch_hx(c->g, c->v, h, s);
+        err = hx_op(c, h, s);
       }
       CU(err, "hx(filter)");
       prev = cur;
@@ -270,7 +270,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
     h.beta = prev ? -sig[k - 1] * sn : 0.0;
     h.E = E;
     h.escale = dpk + (size_t)(k - 1) * ncol;
-    CU(launch_hx(c->g, c->v, h, s), "hx(defect filter)");
+    CU(hx_op(c, h, s), "hx(defect filter)");
     prev = cur;
     cur = Z;
   }
@@ -429,7 +429,7 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const
     a.Z = p;
     a.ncol = n;
     a.shift_col = pl.d_eps_o;
-    CU(launch_hx(c->g, c->v, a, s), "hx(minres)");
+    CU(hx_op(c, a, s), "hx(minres)");
     TRY(project<T>(c, pl, Psi_o, p, s));
     if (sizeof(T) == 8)
       CU(launch_coldot((const double *)z, (const double *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
@@ -610,7 +610,7 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
     a.shift_col = pl.d_eps_o;
     a.W = R;
     a.beta = 1.0;
-    CU(launch_hx(c->g, c->v, a, s), "hx(residual)");
+    CU(hx_op(c, a, s), "hx(residual)");
     TRY(project<double>(c, pl, Psi_o, r64, s));
   }
   // p~ = p_perp + Psi_k d (Eq. 8)

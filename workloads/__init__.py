@@ -188,3 +188,34 @@ def lda_exchange(rho: np.ndarray) -> np.ndarray:
     This is the reference exchange-correlation model of the synthetic workloads
     (an input recipe, not a step of the inverse method)."""
     return -((3.0 / math.pi) ** (1.0 / 3.0)) * np.cbrt(np.maximum(rho, 0.0))
+
+
+MODEL_WIDTH = 1.0      # bohr: width of the Gaussian model density per nucleus
+
+
+def model_fields(wl: Workload, xyz: np.ndarray):
+    """Closed-form input fields of a workload at coordinates xyz [n, 3].
+
+    rho_model: Gaussian charge Z_I of width MODEL_WIDTH on every nucleus;
+    v_H: its exact Hartree potential; v_ext: the smeared nuclei;
+    v_xc_ref: LDA exchange of rho_model, plus the workload's bumps, plus (for
+    the 100-electron case) a -v_H/N_e tail switched on where rho_model is small,
+    f = rho/(rho + 1e-2) -- the form of the paper's initial guess (Sec. 4.2.3)
+    used here only to give the reference potential a -1/r far field.
+    """
+    rho = gaussian_density(xyz, wl.nuclei_R, wl.nuclei_Z, MODEL_WIDTH)
+    v_h = gaussian_density_hartree(xyz, wl.nuclei_R, wl.nuclei_Z, MODEL_WIDTH)
+    v_ext = smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
+    v_xc = lda_exchange(rho) + gaussian_bumps(xyz, wl.bump_c, wl.bump_a, wl.bump_b)
+    if wl.name == "cube32_q4_e100":
+        f = rho / (rho + 1e-2)
+        v_xc = v_xc + (1.0 - f) * (-v_h / wl.n_electrons)
+    return dict(rho_model=rho, v_H=v_h, v_ext=v_ext, v_fixed=v_ext + v_h, v_xc_ref=v_xc)
+
+
+WORKLOADS = {
+    "cube8_q2_he": cube8_q2_he,
+    "cube32_q4_hx": cube32_q4_hx,
+    "cube24_q4_e20": cube24_q4_e20,
+    "cube32_q4_e100": cube32_q4_e100,
+}
