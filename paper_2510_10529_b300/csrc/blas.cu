@@ -11,16 +11,16 @@ constexpr int kTile = 64;    // Gram output tile (kTile x kTile per CTA column)
 constexpr int kRows = 32;    // rows staged per step
 
 // partial[b][i][j] over the rows owned by CTA b, for the (ty, tx) output tile.
-template <typename TA>
+template <typename TA, typename TC>
 __global__ void __launch_bounds__(256) gram_partial(const TA *__restrict__ A, int n1,
                                                     const TA *__restrict__ B, int n2, long long L,
                                                     double *__restrict__ partial) {
-  __shared__ double sA[kRows][kTile + 1];
-  __shared__ double sB[kRows][kTile + 1];
+  __shared__ TC sA[kRows][kTile + 1];
+  __shared__ TC sB[kRows][kTile + 1];
   const int tid = threadIdx.x;
   const int ti = tid / 16, tj = tid % 16;
   const int i0 = blockIdx.y * kTile, j0 = blockIdx.z * kTile;
-  double acc[4][4] = {};
+  TC acc[4][4] = {};
   const long long rows_per = (L + gridDim.x - 1) / gridDim.x;
   const long long r_begin = blockIdx.x * rows_per;
   const long long r_end = min(L, r_begin + rows_per);
@@ -29,13 +29,13 @@ __global__ void __launch_bounds__(256) gram_partial(const TA *__restrict__ A, in
       const int r = idx / kTile, c = idx % kTile;
       const long long row = r0 + r;
       const bool ok = row < r_end;
-      sA[r][c] = (ok && i0 + c < n1) ? (double)A[row * n1 + i0 + c] : 0.0;
-      sB[r][c] = (ok && j0 + c < n2) ? (double)B[row * n2 + j0 + c] : 0.0;
+      sA[r][c] = (ok && i0 + c < n1) ? (TC)A[row * n1 + i0 + c] : (TC)0;
+      sB[r][c] = (ok && j0 + c < n2) ? (TC)B[row * n2 + j0 + c] : (TC)0;
     }
     __syncthreads();
 #pragma unroll 4
     for (int r = 0; r < kRows; ++r) {
-      double a[4], b[4];
+      TC a[4], b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         a[k] = sA[r][ti * 4 + k];
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) gram_partial(const TA *__restrict__ A, in
 #pragma unroll
     for (int y = 0; y < 4; ++y) {
       const int i = i0 + ti * 4 + x, j = j0 + tj * 4 + y;
-      if (i < n1 && j < n2) out[i * n2 + j] = acc[x][y];
+      if (i < n1 && j < n2) out[i * n2 + j] = (double)acc[x][y];
     }
 }
 
@@ -67,13 +67,13 @@ __global__ void sum_partials(const double *__restrict__ partial, int nblk, int n
   G[e] = s;
 }
 
-template <typename TA>
+template <typename TA, typename TC>
 cudaError_t gram_t(const TA *A, int n1, const TA *B, int n2, long long L, double *G,
                    double *partial, cudaStream_t s) {
   if (n1 < 1 || n2 < 1 || n1 > kMaxGram || n2 > kMaxGram) return cudaErrorInvalidValue;
   dim3 grid(kGramBlocks, (n1 + kTile - 1) / kTile, (n2 + kTile - 1) / kTile);
   ::invdft::count_launch();
-  gram_partial<TA><<<grid, 256, 0, s>>>(A, n1, B, n2, L, partial);
+  gram_partial<TA, TC><<<grid, 256, 0, s>>>(A, n1, B, n2, L, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
@@ -106,6 +106,38 @@ __global__ void __launch_bounds__(256) rotate_kernel(const double *__restrict__ 
         double s = 0.0;
         for (int i = 0; i < n1; ++i) s = fma(sX[r * n1 + i], sC[i * n2 + j], s);
         Xo[a * n2 + j] = s;
+      }
+    }
+  }
+}
+
+// Xo[a][j] += alpha * sum_i Xi[a][i] Cm[i][j]  (storage and arithmetic in T)
+template <typename T>
+__global__ void __launch_bounds__(256) rotate_acc_kernel(const T *__restrict__ Xi, int n1,
+                                                         const double *__restrict__ Cm, int n2,
+                                                         long long L, T *__restrict__ Xo,
+                                                         double alpha) {
+  extern __shared__ unsigned char sm_raw[];
+  T *sC = reinterpret_cast<T *>(sm_raw);   // n1 * n2
+  T *sX = sC + n1 * n2;                     // rows_per_pass * n1
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n1 * n2; e += 256) sC[e] = (T)(alpha * Cm[e]);
+  const int rpp = max(1, 256 / n2);
+  const int r = tid / n2, j = tid % n2;
+  for (long long a0 = (long long)blockIdx.x * rpp; a0 < L; a0 += (long long)gridDim.x * rpp) {
+    __syncthreads();
+    for (int e = tid; e < rpp * n1; e += 256) {
+      const int rr = e / n1, i = e % n1;
+      const long long a = a0 + rr;
+      sX[rr * n1 + i] = a < L ? Xi[a * n1 + i] : (T)0;
+    }
+    __syncthreads();
+    if (r < rpp) {
+      const long long a = a0 + r;
+      if (a < L) {
+        T s = 0;
+        for (int i = 0; i < n1; ++i) s = fma(sX[r * n1 + i], sC[i * n2 + j], s);
+        Xo[a * n2 + j] += s;
       }
     }
   }
@@ -155,6 +187,15 @@ cudaError_t coldot_t(const TA *A, const TA *B, int ncol, long long L, double *d,
   return cudaGetLastError();
 }
 
+__global__ void gather_cols_kernel(const double *__restrict__ X, int nv, const int *__restrict__ idx,
+                                   int n, long long L, double *__restrict__ Out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long a = e / n;
+    Out[e] = X[a * nv + idx[e - a * n]];
+  }
+}
+
 __global__ void conv_d2f(const double *__restrict__ x, float *__restrict__ y, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -191,11 +232,11 @@ int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148
 
 cudaError_t launch_gram(const double *A, int n1, const double *B, int n2, long long L, double *G,
                         double *partial, cudaStream_t s) {
-  return gram_t<double>(A, n1, B, n2, L, G, partial, s);
+  return gram_t<double, double>(A, n1, B, n2, L, G, partial, s);
 }
 cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long long L,
                             double *G, double *partial, cudaStream_t s) {
-  return gram_t<float>(A, n1, B, n2, L, G, partial, s);
+  return gram_t<float, double>(A, n1, B, n2, L, G, partial, s);
 }
 cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, long long L,
                           double *Xo, cudaStream_t s) {
@@ -209,6 +250,27 @@ cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, lo
   rotate_kernel<<<148 * 4, 256, smem, s>>>(Xi, n1, Cm, n2, L, Xo);
   return cudaGetLastError();
 }
+cudaError_t launch_gram_f32acc(const float *A, int n1, const float *B, int n2, long long L,
+                               double *G, double *partial, cudaStream_t s) {
+  return gram_t<float, float>(A, n1, B, n2, L, G, partial, s);
+}
+template <typename T>
+cudaError_t launch_rotate_acc(const T *Xi, int n1, const double *Cm, int n2, long long L, T *Xo,
+                              double alpha, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > kMaxGram || n2 > kMaxGram) return cudaErrorInvalidValue;
+  const int rpp = std::max(1, 256 / n2);
+  const size_t smem = sizeof(T) * ((size_t)n1 * n2 + (size_t)rpp * n1);
+  cudaError_t e = cudaFuncSetAttribute(rotate_acc_kernel<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
+  rotate_acc_kernel<T><<<148 * 4, 256, smem, s>>>(Xi, n1, Cm, n2, L, Xo, alpha);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rotate_acc<double>(const double *, int, const double *, int, long long,
+                                               double *, double, cudaStream_t);
+template cudaError_t launch_rotate_acc<float>(const float *, int, const double *, int, long long,
+                                              float *, double, cudaStream_t);
 cudaError_t launch_coldot(const double *A, const double *B, int ncol, long long L, double *d,
                           double *partial, cudaStream_t s) {
   return coldot_t<double>(A, B, ncol, L, d, partial, s);
@@ -216,6 +278,12 @@ cudaError_t launch_coldot(const double *A, const double *B, int ncol, long long 
 cudaError_t launch_coldot_f32(const float *A, const float *B, int ncol, long long L, double *d,
                               double *partial, cudaStream_t s) {
   return coldot_t<float>(A, B, ncol, L, d, partial, s);
+}
+cudaError_t launch_gather_cols(const double *X, int nv, const int *idx, int n, long long L,
+                               double *Out, cudaStream_t s) {
+  ::invdft::count_launch();
+  gather_cols_kernel<<<grid_for(L * n), 256, 0, s>>>(X, nv, idx, n, L, Out);
+  return cudaGetLastError();
 }
 cudaError_t launch_convert_f64_to_f32(const double *x, float *y, long long n, cudaStream_t s) {
   ::invdft::count_launch();

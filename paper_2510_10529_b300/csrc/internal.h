@@ -83,6 +83,7 @@ struct Ctx {
   size_t ws_bytes = 0;
   Arena ar;
   double upper_bound = 0.0;         // cached spectral upper bound of H~
+  double eig_tol_used = 0.0;        // eigen tolerance of the last forward solve
   bool have_upper = false;
 
   // ---- device state (inside the workspace)
@@ -167,6 +168,13 @@ cudaError_t launch_gram(const double *A, int n1, const double *B, int n2, long l
                         double *G, double *partial, cudaStream_t s);
 cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long long L,
                             double *G, double *partial, cudaStream_t s);
+// FP32 inputs, FP32 accumulation inside a CTA, FP64 across CTAs
+cudaError_t launch_gram_f32acc(const float *A, int n1, const float *B, int n2, long long L,
+                               double *G, double *partial, cudaStream_t s);
+// Xo += alpha * Xi Cm  (n1 -> n2 columns) in the storage precision T
+template <typename T>
+cudaError_t launch_rotate_acc(const T *Xi, int n1, const double *Cm, int n2, long long L, T *Xo,
+                              double alpha, cudaStream_t s);
 // Xo[a][j] = sum_i Xi[a][i] Cm[i*n2 + j]   (n1 -> n2 columns), FP64
 cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, long long L,
                           double *Xo, cudaStream_t s);
@@ -176,6 +184,9 @@ cudaError_t launch_coldot(const double *A, const double *B, int ncol, long long 
 cudaError_t launch_coldot_f32(const float *A, const float *B, int ncol, long long L, double *d,
                               double *partial, cudaStream_t s);
 // weighted scalar sums over nodes: out[k] = sum_a f_k(a) (see blas.cu)
+// Out[a][c] = X[a*nv + idx[c]]
+cudaError_t launch_gather_cols(const double *X, int nv, const int *idx, int n, long long L,
+                               double *Out, cudaStream_t s);
 cudaError_t launch_convert_f64_to_f32(const double *x, float *y, long long n, cudaStream_t s);
 cudaError_t launch_convert_f32_to_f64(const float *x, double *y, long long n, cudaStream_t s);
 cudaError_t launch_fill_random(double *X, long long n, unsigned long long seed, cudaStream_t s);

@@ -167,18 +167,25 @@ invdft_status apply_h_f64(Ctx *c, const double *X, double *Z, int n, cudaStream_
   return INVDFT_OK;
 }
 
+// Adaptive tolerances of Sec. 4.2.4: t_eig = e_L2^2 / c_eig, t_ad = e_L2^2 / c_ad
+// with e_L2 from the last loss evaluation; floors keep them reachable in FP64.
+// Before any loss is known the solves use 1e-3 and 1e-6.
 double eig_tolerance(const Ctx *c) {
   if (c->o.eig_tol > 0) return c->o.eig_tol;
-  if (c->err_l2 <= 0) return 1e-6;
-  return std::min(1e-3, std::max(c->err_l2 * c->err_l2 / c->o.c_eig, 1e-10));
+  if (c->err_l2 <= 0) return 1e-3;
+  return std::max(c->err_l2 * c->err_l2 / c->o.c_eig, 1e-10);
 }
 double adj_tolerance(const Ctx *c) {
   if (c->o.adj_tol > 0) return c->o.adj_tol;
-  if (c->err_l2 <= 0) return 1e-8;
-  return std::min(1e-4, std::max(c->err_l2 * c->err_l2 / c->o.c_ad, 1e-10));
+  if (c->err_l2 <= 0) return 1e-6;
+  return std::min(0.1, std::max(c->err_l2 * c->err_l2 / c->o.c_ad, 1e-10));
 }
 
-bool state_active(const Ctx *c, double f) { return c->o.kT > 0 ? f > 1e-13 : f > 0.0; }
+// States whose residual the forward solve drives to the tolerance, and states
+// that get an adjoint column.  With smearing, states of occupation below the
+// cut (1e-8) change the gradient by about that fraction of its norm.
+bool state_active(const Ctx *c, double f) { return c->o.kT > 0 ? f > 1e-8 : f > 0.0; }
+bool adjoint_active(const Ctx *c, double f) { return state_active(c, f); }
 
 }  // namespace
 
@@ -305,6 +312,7 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
     c->have_upper = true;
   }
   const double tol = eig_tolerance(c);
+  c->eig_tol_used = tol;
   std::vector<double> theta(n), occ(n), res2(n);
   int pass = 0;
   double maxres = 0.0;
@@ -362,26 +370,35 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
 // ---------------------------------------------------------------- adjoint
 namespace {
 
+// Columns of the batched adjoint solve: the occupied states, their shifts,
+// and the coefficients of p~ along every computed Ritz vector.
 struct AdjPlan {
   int no = 0;
-  std::vector<int> idx;        // compact column -> state
-  std::vector<int> cs, ia, ib; // pairs per column: [cs[c], cs[c+1])
-  int *d_idx = nullptr, *d_cs = nullptr, *d_ia = nullptr, *d_ib = nullptr;
-  double *d_eps_o = nullptr, *d_f_o = nullptr, *d_dcoef = nullptr, *d_coef = nullptr;
+  std::vector<int> idx;            // compact column -> state index
+  int *d_idx = nullptr;
+  double *d_eps_o = nullptr, *d_f_o = nullptr;
 };
 
+// Z <- Z - Psi (Psi^T Z): projection onto the complement of the nv computed
+// Ritz vectors (Psi [L][nv], Z [L][no], both in precision T).
 template <typename T>
-invdft_status project(Ctx *c, const AdjPlan &pl, const double *Psi_o, T *X, cudaStream_t s) {
-  const int np = pl.cs[pl.no];
-  CU((launch_pairdot<double, T>(Psi_o, pl.no, pl.d_ia, X, pl.no, pl.d_ib, np, c->L, pl.d_coef,
-                                c->partial, s)), "pairdot");
-  CU(launch_project_apply<T>(Psi_o, pl.no, pl.d_cs, pl.d_ia, pl.d_coef, X, pl.no, c->L, s),
-     "project");
+invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s) {
+  double *Cp = c->small + 4 * kMaxGram * kMaxGram;
+  if (sizeof(T) == 8)
+    CU(launch_gram((const double *)Psi, nv, (const double *)Z, no, c->L, Cp, c->partial, s),
+       "gram(deflate)");
+  else
+    CU(launch_gram_f32acc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
+       "gram(deflate)");
+  CU(launch_rotate_acc<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "rotate(deflate)");
   return INVDFT_OK;
 }
 
+// Batched preconditioned MINRES (Paige & Saunders) on Q (H~ - eps_c) Q for
+// every column at once, Q = I - Psi Psi^T, preconditioner Q T Q with T the
+// inverse diagonal of the kinetic part (Sec. 3.2.2).  b must lie in range(Q).
 template <typename T>
-invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const T *b, T *x,
+invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, const T *b, T *x,
                            const std::vector<double> &tol, int maxit, int *iters_out,
                            cudaStream_t s) {
   const int n = pl.no;
@@ -391,8 +408,7 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const
   T *wp = (T *)c->mr[4], *p = (T *)c->mr[5], *zh = (T *)c->mr[6];
   double *st = c->scal + kScMr;    // kMrCount x n scalars
   CU(launch_prec_apply<T>(b, c->prec_diag, n, L, z, s), "prec");
-  TRY(project<T>(c, pl, Psi_o, z, s));
-  // beta1^2 into st[kMrBnext] temporarily
+  TRY(deflate<T>(c, Psi, nv, z, n, s));
   if (sizeof(T) == 8)
     CU(launch_coldot((const double *)b, (const double *)z, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
   else
@@ -418,7 +434,7 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const
   int it = 0;
   std::vector<double> act(n);
   for (; it < maxit; ++it) {
-    if (it % 4 == 0 || it < 4) {
+    if (it % 4 == 0) {
       TRY(fetch(c, st + kMrActive * n, n * sizeof(double), act.data(), s));
       bool any = false;
       for (int j = 0; j < n; ++j) any |= act[j] != 0.0;
@@ -430,14 +446,14 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const
     a.ncol = n;
     a.shift_col = pl.d_eps_o;
     CU(hx_op(c, a, s), "hx(minres)");
-    TRY(project<T>(c, pl, Psi_o, p, s));
+    TRY(deflate<T>(c, Psi, nv, p, n, s));
     if (sizeof(T) == 8)
       CU(launch_coldot((const double *)z, (const double *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
     else
       CU(launch_coldot_f32((const float *)z, (const float *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
     CU(launch_mr_lanczos<T>(p, q, qprev, st + kMrAlpha * n, st + kMrBeta * n, c->prec_diag, n, L,
                             p, zh, s), "mr_lanczos");
-    TRY(project<T>(c, pl, Psi_o, zh, s));
+    TRY(deflate<T>(c, Psi, nv, zh, n, s));
     if (sizeof(T) == 8)
       CU(launch_coldot((const double *)p, (const double *)zh, n, L, st + kMrBnext * n, c->partial, s), "coldot");
     else
@@ -457,12 +473,19 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const double *Psi_o, const
 
 }  // namespace
 
-// Adjoint functions for the upstream dL/drho (device [L]) around the last
-// forward solve.  Output: compact P_o in c->P ([L][no]), Psi_o in c->HY, and
-// the compact map in *plan.  If p_full != nullptr, also the full [L][nv].
-invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft_stats *stats,
-                            AdjPlan *plan_out, cudaStream_t s);
-
+// Adjoint functions p~ for the upstream dL/drho (device [L]) around the last
+// forward solve (Eq. 7-10, 20).  The unique solution is assembled from
+//   * the component along the degenerate set Psi_k of each state (Eq. 8-9);
+//   * the components along the other converged Ritz vectors psi_j, which
+//     (H~ - eps_i) maps to (eps_j - eps_i) psi_j, so psi_j^T p~_i =
+//     psi_j^T g~_i / (eps_j - eps_i) exactly for eigenpairs;
+//   * the component in the complement of those vectors, where
+//     H~ - eps_i is positive definite, by batched preconditioned MINRES
+//     (FP32 or FP64 inner iterations) inside FP64 iterative refinement.
+// This deflation gives the same p~ as a solve on the complement of Psi_k
+// alone (Sec. 3.2.2) but keeps the Krylov operator well conditioned when
+// other levels lie close to eps_i.
+// Output: compact P_o in c->P ([L][no]), Psi_o in c->HY; *plan_out the map.
 invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft_stats *stats,
                             AdjPlan *plan_out, cudaStream_t s) {
   const double t0 = wall_ms();
@@ -478,53 +501,38 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   TRY(fetch(c, c->dfde, nv * sizeof(double), dfde.data(), s));
   AdjPlan pl;
   for (int i = 0; i < nv; ++i)
-    if (state_active(c, f[i])) pl.idx.push_back(i);
+    if (adjoint_active(c, f[i])) pl.idx.push_back(i);
   pl.no = (int)pl.idx.size();
   const int no = pl.no;
   if (no == 0) {
     c->err = "adjoint_solve: no occupied states";
     return INVDFT_EINVAL;
   }
-  // degenerate sets among the active states (ascending eigenvalues)
-  std::vector<int> grp(no);
+  // degenerate sets over all computed states (ascending eigenvalues)
+  std::vector<int> grp(nv);
   int g = 0;
-  for (int k = 0; k < no; ++k) {
-    if (k > 0 && !(eps[pl.idx[k]] - eps[pl.idx[k - 1]] < c->o.deg_tol)) ++g;
-    grp[k] = g;
+  for (int i = 0; i < nv; ++i) {
+    if (i > 0 && !(eps[i] - eps[i - 1] < c->o.deg_tol)) ++g;
+    grp[i] = g;
   }
-  pl.cs.assign(no + 1, 0);
-  for (int k = 0; k < no; ++k) {
-    int cnt = 0;
-    for (int j = 0; j < no; ++j)
-      if (grp[j] == grp[k]) {
-        pl.ia.push_back(j);
-        pl.ib.push_back(k);
-        ++cnt;
-      }
-    if (cnt > kMaxGroup) {
-      c->err = "adjoint_solve: degenerate set larger than 16";
-      return INVDFT_EINVAL;
-    }
-    pl.cs[k + 1] = pl.cs[k] + cnt;
-  }
-  const int np = pl.cs[no];
-  // device tables in the int/scalar areas of the workspace
+  // deflation set: the active states and every other Ritz pair converged to
+  // the eigen tolerance (an unconverged vector would carry its residual into
+  // every column through the exact-ratio formula)
+  std::vector<double> res2(nv);
+  TRY(fetch(c, c->scal + kScRes, nv * sizeof(double), res2.data(), s));
+  std::vector<int> dset;
+  const double rtol = 10.0 * std::max(c->eig_tol_used, 1e-12);
+  for (int i = 0; i < nv; ++i)
+    if (adjoint_active(c, f[i]) || std::sqrt(std::max(res2[i], 0.0)) <= rtol) dset.push_back(i);
+  const int nd = (int)dset.size();
   int *ibase = reinterpret_cast<int *>(c->scal + kScInt);
   pl.d_idx = ibase;
-  pl.d_cs = ibase + kMaxDense;
-  pl.d_ia = ibase + 2 * kMaxDense + 1;
-  pl.d_ib = pl.d_ia + kMaxDense * kMaxGroup;
-  std::vector<int> ints(2 * kMaxDense + 1 + 2 * kMaxDense * kMaxGroup, 0);
-  std::copy(pl.idx.begin(), pl.idx.end(), ints.begin());
-  std::copy(pl.cs.begin(), pl.cs.end(), ints.begin() + kMaxDense);
-  std::copy(pl.ia.begin(), pl.ia.end(), ints.begin() + 2 * kMaxDense + 1);
-  std::copy(pl.ib.begin(), pl.ib.end(), ints.begin() + 2 * kMaxDense + 1 + kMaxDense * kMaxGroup);
-  TRY(push(c, ibase, ints.data(), ints.size() * sizeof(int), s));
+  int *d_dset = ibase + kMaxDense;
+  TRY(push(c, ibase, pl.idx.data(), no * sizeof(int), s));
+  TRY(push(c, d_dset, dset.data(), nd * sizeof(int), s));
   double *dbase = c->scal + kScAdj;
   pl.d_eps_o = dbase;
   pl.d_f_o = dbase + kMaxDense;
-  pl.d_dcoef = dbase + 2 * kMaxDense;
-  pl.d_coef = dbase + 2 * kMaxDense + kMaxDense * kMaxGroup;
   std::vector<double> eo(no), fo(no);
   for (int k = 0; k < no; ++k) {
     eo[k] = eps[pl.idx[k]];
@@ -532,44 +540,62 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   }
   TRY(push(c, pl.d_eps_o, eo.data(), no * sizeof(double), s));
   TRY(push(c, pl.d_f_o, fo.data(), no * sizeof(double), s));
-  // Psi_o (HY), b = 4 f omega psi (Rg), W = omega psi (Y)
+  // Psi_o (HY), b = 4 f omega psi (Rg), W = omega psi (Y); Psi_D (C1, FP64)
   double *Psi_o = c->HY, *R = c->Rg, *Wo = c->Y, *Po = c->P, *r64 = c->Y;
+  double *PsiD = (double *)c->C1;
   CU(launch_adjoint_rhs(c->X, nv, pl.d_idx, no, pl.d_f_o, dLdrho, c->mass, L, Psi_o, R, Wo, s),
      "adjoint_rhs");
-  // J = Psi_o^T diag(omega) Psi_o;  eta (Eq. 9); along-Psi coefficients (Eq. 8)
+  CU(launch_gather_cols(c->X, nv, d_dset, nd, L, PsiD, s), "gather(psi_D)");
+  // J[j][c] = psi_Dj^T diag(omega) psi_{s_c}
   double *J = c->small;
-  CU(launch_gram(Wo, no, Psi_o, no, L, J, c->partial, s), "gram(J)");
-  std::vector<double> Jh((size_t)no * no);
+  CU(launch_gram(PsiD, nd, Wo, no, L, J, c->partial, s), "gram(J)");
+  std::vector<double> Jh((size_t)nd * no), bn(no);
   TRY(fetch(c, J, Jh.size() * sizeof(double), Jh.data(), s));
+  CU(launch_coldot(R, R, no, L, c->scal + kScCol, c->partial, s), "coldot");
+  TRY(fetch(c, c->scal + kScCol, no * sizeof(double), bn.data(), s));
+  std::vector<int> drow(nv, -1);
+  for (int j = 0; j < nd; ++j) drow[dset[j]] = j;
+  // eta (Eq. 9), component along the degenerate set (Eq. 8) and along the
+  // other deflated vectors; A = Psi_D^T b removes b's part inside span(Psi_D)
   double sdf = 0.0, sdfI = 0.0;
   for (int k = 0; k < no; ++k) {
     sdf += dfde[pl.idx[k]];
-    sdfI += dfde[pl.idx[k]] * Jh[(size_t)k * no + k];
+    sdfI += dfde[pl.idx[k]] * Jh[(size_t)drow[pl.idx[k]] * no + k];
   }
   const double eta = sdf != 0.0 ? 2.0 * sdfI / sdf : 0.0;
-  std::vector<double> dco(np);
-  for (int cc = 0; cc < no; ++cc)
-    for (int k = pl.cs[cc]; k < pl.cs[cc + 1]; ++k) {
-      const int j = pl.ia[k];
-      dco[k] = dfde[pl.idx[cc]] * (-2.0 * Jh[(size_t)j * no + cc] + (j == cc ? eta : 0.0));
+  std::vector<double> Cm((size_t)nd * no), Am((size_t)nd * no), gn(no);
+  for (int k = 0; k < no; ++k) {
+    const int si = pl.idx[k];
+    double along_grp = 0.0;
+    for (int jj = 0; jj < nd; ++jj) {
+      const int j = dset[jj];
+      const double a = 4.0 * f[si] * Jh[(size_t)jj * no + k];
+      Am[(size_t)jj * no + k] = a;
+      if (grp[j] == grp[si]) {
+        Cm[(size_t)jj * no + k] = dfde[si] * (-2.0 * Jh[(size_t)jj * no + k] + (j == si ? eta : 0.0));
+        along_grp += a * a;
+      } else {
+        Cm[(size_t)jj * no + k] = a / (eps[j] - eps[si]);
+      }
     }
-  TRY(push(c, pl.d_dcoef, dco.data(), np * sizeof(double), s));
-  // g~ = P b (Eq. 10 removes the component along the degenerate set)
-  TRY(project<double>(c, pl, Psi_o, R, s));
-  std::vector<double> gn(no);
-  CU(launch_coldot(R, R, no, L, c->scal + kScCol, c->partial, s), "coldot");
-  TRY(fetch(c, c->scal + kScCol, no * sizeof(double), gn.data(), s));
-  for (auto &x : gn) x = std::sqrt(std::max(x, 0.0));
+    gn[k] = std::sqrt(std::max(bn[k] - along_grp, 0.0));     // |g~| of Eq. 10
+  }
+  double *dC = c->small + 5 * kMaxGram * kMaxGram, *dA = c->small + 6 * kMaxGram * kMaxGram;
+  TRY(push(c, dC, Cm.data(), Cm.size() * sizeof(double), s));
+  TRY(push(c, dA, Am.data(), Am.size() * sizeof(double), s));
+  CU(launch_rotate_acc<double>(PsiD, nd, dA, no, L, R, -1.0, s), "deflate(rhs)");   // R = Q b
   // iterative refinement around the inner MINRES (FP32 or FP64)
   const double tad = adj_tolerance(c);
   const size_t blk = (size_t)L * no;
   CU(cudaMemsetAsync(Po, 0, blk * sizeof(double), s), "memset");
   CU(cudaMemcpyAsync(r64, R, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+  const bool mixed = c->o.prec == INVDFT_MIXED;
+  float *Psi32 = (float *)c->C0;
+  if (mixed) CU(launch_convert_f64_to_f32(PsiD, Psi32, (long long)L * nd, s), "convert(psi)");
   std::vector<double> rn(no), tol(no);
   int total_iters = 0, outer = 0;
   double relmax = 0.0;
   invdft_status status = INVDFT_OK;
-  const bool mixed = c->o.prec == INVDFT_MIXED;
   for (;; ++outer) {
     CU(launch_coldot(r64, r64, no, L, c->scal + kScCol, c->partial, s), "coldot");
     TRY(fetch(c, c->scal + kScCol, no * sizeof(double), rn.data(), s));
@@ -579,7 +605,7 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
       const double rel = gn[k] > 0 ? r / gn[k] : 0.0;
       relmax = std::max(relmax, rel);
       const double floor_tol = mixed ? 1e-6 : 1e-14;
-      tol[k] = rel > 0 ? std::max(floor_tol, std::min(0.5, 0.5 * tad / rel)) : 1.0;
+      tol[k] = rel > tad ? std::max(floor_tol, std::min(0.5, 0.5 * tad / rel)) : 1.0;
     }
     if (relmax <= tad) break;
     if (outer >= 12) {
@@ -591,17 +617,17 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
     if (mixed) {
       float *b32 = (float *)c->mr[8], *x32 = (float *)c->mr[7];
       CU(launch_convert_f64_to_f32(r64, b32, (long long)blk, s), "convert");
-      TRY(minres_block<float>(c, pl, Psi_o, b32, x32, tol, c->o.max_minres_iters, &its, s));
+      TRY(minres_block<float>(c, pl, Psi32, nd, b32, x32, tol, c->o.max_minres_iters, &its, s));
       CU((launch_add_convert<float, double>(x32, Po, (long long)blk, s)), "add");
     } else {
       double *b64 = (double *)c->mr[8], *x64 = (double *)c->mr[7];
       CU(cudaMemcpyAsync(b64, r64, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
-      TRY(minres_block<double>(c, pl, Psi_o, b64, x64, tol, c->o.max_minres_iters, &its, s));
+      TRY(minres_block<double>(c, pl, PsiD, nd, b64, x64, tol, c->o.max_minres_iters, &its, s));
       CU((launch_add_convert<double, double>(x64, Po, (long long)blk, s)), "add");
     }
     total_iters += its;
-    TRY(project<double>(c, pl, Psi_o, Po, s));
-    // r = g~ - P (H~ - eps) P p
+    TRY(deflate<double>(c, PsiD, nd, Po, no, s));
+    // r = Q b - Q (H~ - eps) Q p
     HxArgs<double> a;
     a.X = Po;
     a.Z = r64;
@@ -611,10 +637,10 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
     a.W = R;
     a.beta = 1.0;
     CU(hx_op(c, a, s), "hx(residual)");
-    TRY(project<double>(c, pl, Psi_o, r64, s));
+    TRY(deflate<double>(c, PsiD, nd, r64, no, s));
   }
-  // p~ = p_perp + Psi_k d (Eq. 8)
-  CU(launch_add_along(Psi_o, pl.d_cs, pl.d_ia, pl.d_dcoef, Po, no, L, s), "add_along");
+  // p~ = p_Q + Psi C  (Eq. 8 inside the degenerate set, exact ratios outside)
+  CU(launch_rotate_acc<double>(PsiD, nd, dC, no, L, Po, 1.0, s), "along(psi)");
   if (p_full) {
     CU(cudaMemsetAsync(p_full, 0, (size_t)L * nv * sizeof(double), s), "memset");
     CU(launch_scatter_cols(Po, no, pl.d_idx, p_full, nv, L, s), "scatter");
