@@ -206,6 +206,34 @@ invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const dou
 invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out8);
 invdft_status invdft_kernel_launches(unsigned long long *count);
 
+/* Allocation-free loss reduction.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory -- a host
+ * application that owns all device memory through its own fixed pool and
+ * forbids further cudaMalloc/cudaFree (to keep its footprint fixed, or
+ * because an allocation would synchronise the device in the middle of its
+ * pipeline), or a caller that simply has no workspace to bind.  It computes,
+ * like the reduction inside invdft_loss_grad,
+ *   out3[0] = sum_a m_a w_a (rho_data_a - rho_a)^2   (the loss, Eq. 1),
+ *   out3[1] = sum_a m_a (rho_data_a - rho_a)^2       (e_L2^2, Sec. 4.2.4),
+ *   out3[2] = sum_a m_a rho_a                        (N_e, Eq. 5),
+ * and, if dLdrho != NULL, dLdrho_a = -2 m_a w_a (rho_data_a - rho_a).
+ * All arrays are device arrays of length L (out3: 3 doubles) owned by the
+ * caller; w may be NULL (w = 1).  No handle is needed.
+ * Scratch: a fixed 192 KiB device array inside the library, which every GPU
+ * that loads the library keeps until the process exits; it holds one partial
+ * sum per 4096 nodes, so L is limited to 33,554,432 (larger L returns
+ * INVDFT_EINVAL with a message in invdft_last_error(NULL)).  Every partial
+ * used is rewritten by each call, so nothing needs clearing between calls,
+ * and the array keeps the last call's partials afterwards.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls share the one array: calls that may overlap on the GPU
+ * (different streams, or different host threads) race and must be serialised
+ * by the caller.  The call allocates nothing and is asynchronous on stream. */
+invdft_status invdft_loss_reduce_noalloc(const double *rho, const double *rho_data,
+                                         const double *w, const double *mass, long long L,
+                                         double *out3, double *dLdrho, void *stream);
+
 /* Forget the L-BFGS history and the warm-start orbitals.                   */
 invdft_status invdft_reset(invdft_handle h);
 

@@ -80,6 +80,7 @@ def _load():
         "invdft_reset": [H],
         "invdft_profile_hx": [H, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
+        "invdft_loss_reduce_noalloc": [P, P, P, P, C.c_longlong, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

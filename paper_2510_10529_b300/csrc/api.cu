@@ -19,6 +19,7 @@ static thread_local std::string g_create_error;
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void set_global_error(const char *msg) { g_create_error = msg; }
 
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what) {
   if (e == cudaSuccess) return true;
