@@ -65,10 +65,13 @@ typedef enum {
 
 typedef enum {
   INVDFT_FP64 = 0,      /* every step in FP64                                     */
-  INVDFT_MIXED = 1      /* FP32 storage, TF32 tensor-core cell products with FP32
-                           accumulation in the Chebyshev filter and the inner
-                           MINRES iterations; FP64 for Rayleigh-Ritz, Cholesky,
+  INVDFT_MIXED = 1,     /* FP32 storage, TF32 tensor-core cell products with FP32
+                           accumulation (Q4 meshes; FP32 CUDA cores for Q2) in
+                           the Chebyshev filter and the inner MINRES
+                           iterations; FP64 for Rayleigh-Ritz, Cholesky,
                            residuals, refinement and every reduction             */
+  INVDFT_FP32 = 2       /* as MIXED but the FP32 cell products run on the CUDA
+                           cores in FP32 (no TF32 rounding)                      */
 } invdft_precision;
 
 /* Mesh: box [lo,hi]^3, ncell cells per axis, element order (2 or 4). */
@@ -139,7 +142,9 @@ invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed_dev,
                                    const double *v_xc_dev, void *stream);
 
 /* Y = H~ X for an [L][ncol] block (Eq. 19, Sec. 3.2.3), device pointers.
- * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED: X, Y are float.
+ * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED (TF32 tensor cores on
+ * Q4 meshes) or INVDFT_FP32 (FP32 CUDA cores): X, Y are float.  Y must not
+ * alias X.
  * ncol in [1, 256].  The operator used is the one of the last
  * invdft_set_potential.                                                     */
 invdft_status invdft_apply_h(invdft_handle h, const void *X_dev, void *Y_dev, int ncol,

@@ -85,8 +85,10 @@ def invdft_set_potential(h, v_fixed: torch.Tensor, v_xc: torch.Tensor | None):
                lib.invdft_set_potential(h, _ptr(v_fixed), _ptr(v_xc), _stream()), h, False)
 
 
-def invdft_apply_h(h, X: torch.Tensor, Y: torch.Tensor):
-    prec = INVDFT_FP64 if X.dtype == torch.float64 else INVDFT_MIXED
+def invdft_apply_h(h, X: torch.Tensor, Y: torch.Tensor, tensor_cores: bool = True):
+    """Y = H~ X.  float64 blocks run in FP64; float32 blocks on the TF32 tensor
+    cores (Q4 meshes) or, with tensor_cores=False, in FP32 on the CUDA cores."""
+    prec = INVDFT_FP64 if X.dtype == torch.float64 else (INVDFT_MIXED if tensor_cores else 2)
     if X.dtype != Y.dtype or X.dtype not in (torch.float64, torch.float32):
         raise ValueError("apply_h: X and Y must both be float64 or both float32")
     ncol = X.shape[1] if X.dim() == 2 else 1
@@ -171,7 +173,8 @@ class Problem:
                     eig_tol=float(eig_tol), adj_tol=float(adj_tol),
                     max_cheb_passes=int(max_cheb_passes), max_minres_iters=int(max_minres_iters),
                     lbfgs_history=int(lbfgs_history),
-                    prec=INVDFT_MIXED if prec == "mixed" else INVDFT_FP64, seed=int(seed),
+                    prec={"mixed": INVDFT_MIXED, "fp32": 2}.get(prec, INVDFT_FP64),
+                    seed=int(seed),
                     deg_tol=float(deg_tol))
         self.h, self.L = invdft_create_mesh(mesh, opts)
         self.nstates = int(nstates)
@@ -209,9 +212,9 @@ class Problem:
         self.v_fixed = v_fixed
         self.potential_version += 1
 
-    def apply_h(self, X):
+    def apply_h(self, X, tensor_cores: bool = True):
         Y = torch.empty_like(X)
-        invdft_apply_h(self.h, X, Y)
+        invdft_apply_h(self.h, X, Y, tensor_cores)
         return Y
 
     def chebyshev_filter(self, X, degree, a, b, a0):

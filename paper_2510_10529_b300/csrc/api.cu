@@ -71,6 +71,7 @@ size_t plan(Ctx *c, char *base) {
   c->mass = ar.take<double>(L);
   c->dvec = ar.take<double>(L);
   c->prec_diag = ar.take<double>(L);
+  c->Ke_tc = ar.take<float>(tc_cell_matrix_floats());
   c->v = ar.take<double>(L);
   c->vfixed = ar.take<double>(L);
   c->rho = ar.take<double>(L);
@@ -209,6 +210,15 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   ::invdft::count_launch();
   init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag);
   INV_LAUNCH(h, "init_fields");
+  std::vector<float> ke;
+  if (h->g.p == 4) {
+    build_tc_cell_matrix(h->g, &ke);
+    INV_CUDA(h, cudaMemcpyAsync(h->Ke_tc, ke.data(), ke.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, s));
+  } else {
+    h->Ke_tc = nullptr;
+  }
+  INV_CUDA(h, cudaMemsetAsync(h->status, 0, 16 * sizeof(int), s));
   INV_CUDA(h, cudaMemsetAsync(h->v, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaMemsetAsync(h->vfixed, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaStreamSynchronize(s));   // host tables above are freed on return
@@ -291,6 +301,7 @@ invdft_status invdft_apply_h(invdft_handle h, const void *X, void *Y, int ncol,
     a.X = (const float *)X;
     a.Z = (float *)Y;
     a.ncol = ncol;
+    a.tc = prec == INVDFT_MIXED;
     e = hx_op(h, a, s);
   }
   if (!cuda_ok(h, e, "apply_h")) return INVDFT_ECUDA;

@@ -209,10 +209,23 @@ cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cu
 namespace invdft {
 namespace {
 
+// route an FP32 block to the tensor-core kernel when the mesh is Q4, the
+// caller asked for it and the output does not alias an input (the kernel
+// zeroes Z before accumulating into it)
+cudaError_t dispatch_hx(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
+  return launch_hx(c->g, c->v, a, s);
+}
+cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
+  const bool tc = a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
+                  (const void *)a.Z != (const void *)a.E;
+  if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->status + 8, s);
+  return launch_hx(c->g, c->v, a, s);
+}
+
 template <typename T>
 cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   HxProf &p = c->prof;
-  if (!p.on) return launch_hx(c->g, c->v, a, s);
+  if (!p.on) return dispatch_hx(c, a, s);
   const int slots = 1024;
   if (p.ev.empty()) {
     p.ev.resize(2 * slots);
@@ -239,7 +252,7 @@ cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   p.bytes[k] = bytes;
   p.flops[k] = 2.0 * ne * ne * n * cells;
   cudaEventRecord(p.ev[2 * k], s);
-  cudaError_t r = launch_hx(c->g, c->v, a, s);
+  cudaError_t r = dispatch_hx(c, a, s);
   cudaEventRecord(p.ev[2 * k + 1], s);
   return r;
 }

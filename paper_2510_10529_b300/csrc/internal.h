@@ -92,6 +92,7 @@ struct Ctx {
   double *mass = nullptr;           // [L]
   double *dvec = nullptr;           // [L]  m^-1/2
   double *prec_diag = nullptr;      // [L]  1 / diag(D K D)
+  float *Ke_tc = nullptr;           // 128 x 128 TF32 cell matrix in the UMMA layout (Q4)
   double *v = nullptr;              // [L]  total potential
   double *vfixed = nullptr;         // [L]
   double *X = nullptr;              // [L][nv] orbitals (FP64)
@@ -154,6 +155,7 @@ struct HxArgs {
   double beta = 0.0;
   const float *E = nullptr;
   const double *escale = nullptr;
+  bool tc = true;            // FP32 blocks: TF32 tensor-core path where available
 };
 cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<double> &a, cudaStream_t s);
 cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cudaStream_t s);
@@ -161,6 +163,11 @@ cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cu
 cudaError_t hx_op(Ctx *c, const HxArgs<double> &a, cudaStream_t s);
 cudaError_t hx_op(Ctx *c, const HxArgs<float> &a, cudaStream_t s);
 cudaError_t prof_flush(Ctx *c);
+// tensor-core (tcgen05, TF32) H~X for Q4 cells (hx_tc.cu)
+void build_tc_cell_matrix(const Geom &g, std::vector<float> *out);
+size_t tc_cell_matrix_floats();
+cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
+                         int *err, cudaStream_t s);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).

@@ -28,6 +28,9 @@ constexpr size_t kScMr = 256 * (size_t)kMaxCols;    // MINRES scalars
 constexpr size_t kScInt = 400 * (size_t)kMaxCols;   // adjoint int tables
 constexpr size_t kScPk = 512 * (size_t)kMaxCols;    // Chebyshev p_k(theta) table
 
+inline void set_tc(HxArgs<double> &, bool) {}
+inline void set_tc(HxArgs<float> &a, bool on) { a.tc = on; }
+
 // per-column MINRES scalars, st[k * n + c]
 enum { kMrAlpha = 0, kMrBeta, kMrBnext, kMrCpp, kMrSpp, kMrCp, kMrSp, kMrPhibar, kMrBeta1,
        kMrActive, kMrEps, kMrDel, kMrIg, kMrT, kMrIb, kMrRel, kMrTol, kMrIters, kMrCount };
@@ -221,6 +224,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
         err = hx_op(c, h, s);
       } else {
         HxArgs<float> h;
+        h.tc = c->o.prec == INVDFT_MIXED;
         h.X = (const float *)cur;
         h.Z = (float *)Z;
         h.ncol = ncol;
@@ -268,6 +272,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
     const double sn = sig[k];
     void *Z = free_buf(prev, cur);
     HxArgs<float> h;
+    h.tc = c->o.prec == INVDFT_MIXED;
     h.X = (const float *)cur;
     h.Z = (float *)Z;
     h.ncol = ncol;
@@ -441,6 +446,7 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, cons
       if (!any) break;
     }
     HxArgs<T> a;
+    set_tc(a, c->o.prec == INVDFT_MIXED);
     a.X = z;
     a.Z = p;
     a.ncol = n;
@@ -589,7 +595,7 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   const size_t blk = (size_t)L * no;
   CU(cudaMemsetAsync(Po, 0, blk * sizeof(double), s), "memset");
   CU(cudaMemcpyAsync(r64, R, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
-  const bool mixed = c->o.prec == INVDFT_MIXED;
+  const bool mixed = c->o.prec != INVDFT_FP64;
   float *Psi32 = (float *)c->C0;
   if (mixed) CU(launch_convert_f64_to_f32(PsiD, Psi32, (long long)L * nd, s), "convert(psi)");
   std::vector<double> rn(no), tol(no);

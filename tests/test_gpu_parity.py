@@ -2,8 +2,12 @@
 
 Tolerances (stated per result):
   H~X FP64: max over columns of ||Y_gpu - Y_ora|| / ||Y_ora|| <= 1e-10;
-  H~X FP32 storage / FP32 accumulation: same norm <= 2e-6 (u_32 times a small
-    growth factor of the 7 one-dimensional contractions and the assembly sum);
+  H~X FP32 storage / FP32 accumulation on the CUDA cores: same norm <= 2e-6
+    (u_32 times a small growth factor of the 7 one-dimensional contractions
+    and the assembly sum);
+  H~X TF32 tensor cores (Q4): same norm <= 5e-3 (operands rounded to 11
+    significant bits, 2^-11 ~ 4.9e-4 per factor, summed over 125 products with
+    the cancellation of the zero row sums of K_e);
   eigenvalues of occupied states: |d eps| <= 1e-6 Ha;
   density: sqrt(sum_a m_a (rho_gpu - rho_ora)^2) <= 1e-6;
   gradient: ||g_gpu - g_ora|| / ||g_ora|| <= 1e-5.
@@ -59,12 +63,18 @@ def test_apply_h_fp64_and_fp32_match_oracle(geom, ncol):
     pb.set_potential(_cuda(v))
     Y64 = pb.apply_h(_cuda(X)).cpu().numpy()
     assert _colrel(Y64, Y_ora) <= 1e-10
-    Y32 = pb.apply_h(_cuda(X, torch.float32)).double().cpu().numpy()
+    Y32 = pb.apply_h(_cuda(X, torch.float32), tensor_cores=False).double().cpu().numpy()
     assert _colrel(Y32, Y_ora) <= 2e-6
+    Ytc = pb.apply_h(_cuda(X, torch.float32), tensor_cores=True).double().cpu().numpy()
+    err_tc = _colrel(Ytc, Y_ora)
+    print(f"TF32 H~X rel err {err_tc:.3e} (p={p}, ncol={ncol})")
+    assert err_tc <= (5e-3 if p == 4 else 2e-6)
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 2e-6)])
-def test_apply_h_full_size_sampled_rows(dtype, tol):
+@pytest.mark.parametrize("dtype,tc,tol", [(torch.float64, False, 1e-10),
+                                          (torch.float32, False, 2e-6),
+                                          (torch.float32, True, 5e-3)])
+def test_apply_h_full_size_sampled_rows(dtype, tc, tol):
     """The 32^3-cell Q4 operator benchmark (2,048,383 unknowns, 64 columns) in the
     launch configuration the benchmark times; 48 sampled rows against the
     oracle's row-wise definition."""
@@ -75,7 +85,7 @@ def test_apply_h_full_size_sampled_rows(dtype, tol):
     v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
     pb.set_potential(_cuda(v))
     X = _cuda(W.random_block(mesh.L, 64, wl.seed), dtype)
-    Y = pb.apply_h(X)
+    Y = pb.apply_h(X, tensor_cores=tc)
     rng = np.random.default_rng(7)
     rows = np.concatenate([rng.integers(0, mesh.L, 44), [0, mesh.L - 1, mesh.Ni - 1, mesh.L // 2]])
     Xd = X.double()
@@ -86,6 +96,7 @@ def test_apply_h_full_size_sampled_rows(dtype, tol):
     Yo = fe.htilde_rows(mesh, v[rows], rows, fetch)
     Yg = Y[torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
     err = np.linalg.norm(Yg - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
+    print(f"sampled rows {dtype} tc={tc}: max rel err {err.max():.3e}")
     assert err.max() <= tol
 
 
@@ -103,7 +114,7 @@ def test_chebyshev_filter_matches_oracle(cube8):
     assert _colrel(Yg, Y_ora) <= 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
 def test_forward_solve_matches_oracle(cube8, prec):
     wl, mesh, d = cube8
     v = d["v_fixed"] + d["v_xc_ref"]
@@ -203,4 +214,32 @@ def test_autograd_backward_is_the_adjoint(cube8):
                          kT=wl.kT, tau_bc=-1.0)
     _, _, g_ora, _ = inverse.evaluate(op, 0.5 * d["v_xc_ref"])
     g = v_xc.grad.cpu().numpy()
+    assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_q4_mixed_solvers_match_oracle(prec):
+    """Forward solve and gradient on a Q4 mesh, where the mixed path runs its
+    FP32 cell products on the TF32 tensor cores (prec="mixed") or on the CUDA
+    cores (prec="fp32"); tolerances as above."""
+    mesh = fe.Mesh(-6.0, 6.0, 4, 4)
+    xyz = mesh.coords()
+    v = W.smeared_coulomb(xyz, np.array([[0.2, -0.3, 0.1]]), np.array([2.0]), 0.5)
+    bump = 0.1 * np.exp(-np.sum((xyz - 0.5) ** 2, 1))
+    Ne, nst = 2.0, 6
+    rho_d = ks.forward(mesh, v + bump, Ne, nst, 0.0)["rho"]
+    op = inverse.Problem(mesh=mesh, v_fixed=v, rho_data=rho_d, w=np.ones(mesh.L),
+                         n_electrons=Ne, nstates=nst, kT=0.0)
+    v_xc = 0.5 * bump
+    L_ora, e_ora, g_ora, fw_ora = inverse.evaluate(op, v_xc)
+    pb = _problem(-6.0, 6.0, 4, 4, nstates=nst, n_electrons=Ne, kT=0.0, prec=prec,
+                  eig_tol=1e-10, adj_tol=1e-11, cheb_degree=20)
+    pb.set_potential(_cuda(v), _cuda(v_xc))
+    out = pb.forward_solve()
+    assert abs(out["eps"].cpu().numpy()[0] - fw_ora["eps"][0]) <= 1e-6
+    m = mesh.mass()
+    assert math.sqrt(np.sum(m * (out["rho"].cpu().numpy() - fw_ora["rho"]) ** 2)) <= 1e-6
+    loss, g, st = pb.loss_grad(_cuda(rho_d), _cuda(np.ones(mesh.L)))
+    g = g.cpu().numpy()
+    assert abs(loss - L_ora) <= 1e-8 * L_ora
     assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
