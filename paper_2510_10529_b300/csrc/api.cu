@@ -65,6 +65,7 @@ size_t plan(Ctx *c, char *base) {
   const int N = c->g.Ni + 2;
   const size_t blk = (size_t)L * nv;
   c->dm1 = ar.take<double>(N);
+  c->dm1f = ar.take<float>(N);
   c->m1tab = ar.take<double>(N);
   c->kAtab = ar.take<double>(N);
   c->kBtab = ar.take<double>(N);
@@ -72,6 +73,7 @@ size_t plan(Ctx *c, char *base) {
   c->dvec = ar.take<double>(L);
   c->prec_diag = ar.take<double>(L);
   c->Ke_tc = ar.take<float>(tc_cell_matrix_floats());
+  c->cell_perm = ar.take<int>((size_t)c->g.ncell * c->g.ncell * c->g.ncell);
   c->v = ar.take<double>(L);
   c->vfixed = ar.take<double>(L);
   c->rho = ar.take<double>(L);
@@ -204,6 +206,8 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   }
   double *m1 = h->m1tab, *kA = h->kAtab, *kB = h->kBtab;
   INV_CUDA(h, cudaMemcpyAsync(h->dm1, dm1.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<float> dm1f(dm1.begin(), dm1.end());
+  INV_CUDA(h, cudaMemcpyAsync(h->dm1f, dm1f.data(), N * sizeof(float), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(m1, tabs.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(kA, tabs.data() + N, N * sizeof(double), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(kB, tabs.data() + 2 * N, N * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -211,9 +215,13 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag);
   INV_LAUNCH(h, "init_fields");
   std::vector<float> ke;
+  std::vector<int> perm;
   if (h->g.p == 4) {
     build_tc_cell_matrix(h->g, &ke);
     INV_CUDA(h, cudaMemcpyAsync(h->Ke_tc, ke.data(), ke.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, s));
+    build_cell_order(h->g.ncell, &perm);
+    INV_CUDA(h, cudaMemcpyAsync(h->cell_perm, perm.data(), perm.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, s));
   } else {
     h->Ke_tc = nullptr;
@@ -223,6 +231,7 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   INV_CUDA(h, cudaMemsetAsync(h->vfixed, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaStreamSynchronize(s));   // host tables above are freed on return
   h->g.dm1 = h->dm1;
+  h->g.dm1f = h->dm1f;
   h->bound = true;
   h->have_potential = false;
   h->have_orbitals = false;

@@ -218,7 +218,7 @@ cudaError_t dispatch_hx(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
   const bool tc = a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
                   (const void *)a.Z != (const void *)a.E;
-  if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->status + 8, s);
+  if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + 8, s);
   return launch_hx(c->g, c->v, a, s);
 }
 

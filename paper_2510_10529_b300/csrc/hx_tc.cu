@@ -75,6 +75,7 @@ struct TcArgs {
   const double *escale;
   const float *Ke;          // 128 x 128 tf32 in the UMMA layout (kc included)
   const double *dm1;
+  const int *perm;          // visiting order of the cells
   int *err;                 // device status word (set on a timed-out wait)
   double alpha, shift, beta;
   int ncol, ncell, Ni;
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) hx_tc_kernel(TcArgs p) {
     const int c0 = chunk * C;
     if (tid < G * 15) {
       const int g = tid / 15, d = (tid % 15) / 5, l = tid % 5;
-      const long long cell = grp * G + g;
+      const long long slot = grp * G + g;
+      const long long cell = slot < ncells ? p.perm[slot] : ncells;
       int gidx = -1;
       double dv = 0.0;
       if (cell < ncells) {
@@ -397,8 +399,24 @@ void build_tc_cell_matrix(const Geom &g, std::vector<float> *out) {
 
 size_t tc_cell_matrix_floats() { return (size_t)kTcM * kTcK; }
 
+// Cell visiting order: z-slabs two cells thick; inside a slab the 8 parity
+// classes (cx, cy, cz mod 2) one after the other.  Cells in flight at the same
+// time then share no nodes (their reductions do not contend for the same L2
+// lines) while the slab keeps the touched nodes inside L2.
+void build_cell_order(int nc, std::vector<int> *perm) {
+  perm->clear();
+  for (int zs = 0; zs < nc; zs += 2)
+    for (int color = 0; color < 8; ++color)
+      for (int cz = zs; cz < std::min(nc, zs + 2); ++cz)
+        for (int cy = 0; cy < nc; ++cy)
+          for (int cx = 0; cx < nc; ++cx)
+            if ((cx & 1) == (color & 1) && (cy & 1) == ((color >> 1) & 1) &&
+                (cz & 1) == ((color >> 2) & 1))
+              perm->push_back(cx + nc * (cy + nc * cz));
+}
+
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
-                         int *err, cudaStream_t s) {
+                         const int *perm, int *err, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.Z, 0, (size_t)g.L * a.ncol * sizeof(float), s);
   if (e != cudaSuccess) return e;
   const size_t smem = kSmemA + kSmemB;
@@ -425,6 +443,7 @@ cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a,
   p.escale = a.escale;
   p.Ke = Ke;
   p.dm1 = g.dm1;
+  p.perm = perm;
   p.err = err;
   p.alpha = a.alpha;
   p.shift = a.shift;

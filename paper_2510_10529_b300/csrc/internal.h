@@ -30,6 +30,7 @@ struct Geom {
   double A[kMaxQ * kMaxQ];
   double B[kMaxQ * kMaxQ];
   const double *dm1;        // device [Ni + 2]: 1/sqrt(m1) along one axis (0 at the ends)
+  const float *dm1f;        // the same table in FP32 (tensor-core path)
 };
 
 // Host-side FE tables (tables.cu).
@@ -88,11 +89,13 @@ struct Ctx {
 
   // ---- device state (inside the workspace)
   double *dm1 = nullptr;            // [Ni+2]
+  float *dm1f = nullptr;            // [Ni+2] FP32 copy
   double *m1tab = nullptr, *kAtab = nullptr, *kBtab = nullptr;  // [Ni+2] 1D tables
   double *mass = nullptr;           // [L]
   double *dvec = nullptr;           // [L]  m^-1/2
   double *prec_diag = nullptr;      // [L]  1 / diag(D K D)
   float *Ke_tc = nullptr;           // 128 x 128 TF32 cell matrix in the UMMA layout (Q4)
+  int *cell_perm = nullptr;         // [ncell^3] visiting order of the tensor-core kernel
   double *v = nullptr;              // [L]  total potential
   double *vfixed = nullptr;         // [L]
   double *X = nullptr;              // [L][nv] orbitals (FP64)
@@ -167,7 +170,8 @@ cudaError_t prof_flush(Ctx *c);
 void build_tc_cell_matrix(const Geom &g, std::vector<float> *out);
 size_t tc_cell_matrix_floats();
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
-                         int *err, cudaStream_t s);
+                         const int *perm, int *err, cudaStream_t s);
+void build_cell_order(int nc, std::vector<int> *perm);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).
