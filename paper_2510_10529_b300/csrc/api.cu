@@ -126,6 +126,10 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
     g_create_error = "create_mesh: mesh has no unknowns or is too large";
     return INVDFT_EINVAL;
   }
+  if (Ni * Ni * Ni * (long long)kMaxCols >= (1LL << 31)) {
+    g_create_error = "create_mesh: (ncell*order-1)^3 * 256 must stay below 2^31";
+    return INVDFT_EINVAL;
+  }
   if (opts->nstates < 1 || opts->nstates > kMaxDense) {
     g_create_error = "create_mesh: nstates must be in [1, 96]";
     return INVDFT_EINVAL;

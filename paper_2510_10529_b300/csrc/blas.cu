@@ -8,6 +8,7 @@ namespace invdft {
 namespace {
 
 constexpr int kTile = 64;    // Gram output tile (kTile x kTile per CTA column)
+constexpr int kColdotBlocks = 148 * 8;   // column-dot partials (more CTAs in flight)
 constexpr int kRows = 32;    // rows staged per step
 
 // partial[b][i][j] over the rows owned by CTA b, for the (ty, tx) output tile.
@@ -58,6 +59,20 @@ __global__ void __launch_bounds__(256) gram_partial(const TA *__restrict__ A, in
     }
 }
 
+// out[e] = sum_b partial[b * stride + e]: one warp per output, lanes take the
+// blocks b = lane (mod 32), then a fixed shuffle tree (bitwise reproducible)
+__global__ void warp_sum_partials(const double *__restrict__ partial, int nblk, size_t stride,
+                                  int n, double *__restrict__ out) {
+  const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[(size_t)b * stride + e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[e] = s;
+}
+
 __global__ void sum_partials(const double *__restrict__ partial, int nblk, int n1, int n2,
                              double *__restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,7 +92,8 @@ cudaError_t gram_t(const TA *A, int n1, const TA *B, int n2, long long L, double
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
-  sum_partials<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, n1, n2, G);
+  warp_sum_partials<<<(n1 * n2 + 7) / 8, 256, 0, s>>>(partial, kGramBlocks, (size_t)n1 * n2,
+                                                      n1 * n2, G);
   return cudaGetLastError();
 }
 
@@ -153,8 +169,21 @@ __global__ void __launch_bounds__(256) coldot_partial(const TA *__restrict__ A,
   const int j = tid % ncol, r0 = tid / ncol;
   double s = 0.0;
   if (r0 < R) {
-    for (long long a = (long long)blockIdx.x * R + r0; a < L; a += (long long)gridDim.x * R)
-      s += (double)A[a * ncol + j] * (double)B[a * ncol + j];
+    const long long step = (long long)gridDim.x * R;
+    long long a = (long long)blockIdx.x * R + r0;
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (; a + 3 * step < L; a += 4 * step) {
+      const TA x0 = A[a * ncol + j], x1 = A[(a + step) * ncol + j];
+      const TA x2 = A[(a + 2 * step) * ncol + j], x3 = A[(a + 3 * step) * ncol + j];
+      const TA y0 = B[a * ncol + j], y1 = B[(a + step) * ncol + j];
+      const TA y2 = B[(a + 2 * step) * ncol + j], y3 = B[(a + 3 * step) * ncol + j];
+      s += (double)x0 * (double)y0;
+      s1 += (double)x1 * (double)y1;
+      s2 += (double)x2 * (double)y2;
+      s3 += (double)x3 * (double)y3;
+    }
+    for (; a < L; a += step) s += (double)A[a * ncol + j] * (double)B[a * ncol + j];
+    s += (s1 + s2) + s3;
   }
   red[tid] = s;
   __syncthreads();
@@ -179,20 +208,20 @@ cudaError_t coldot_t(const TA *A, const TA *B, int ncol, long long L, double *d,
                      cudaStream_t s) {
   if (ncol < 1 || ncol > kMaxCols) return cudaErrorInvalidValue;
   ::invdft::count_launch();
-  coldot_partial<TA><<<kGramBlocks, 256, 0, s>>>(A, B, ncol, L, partial);
+  coldot_partial<TA><<<kColdotBlocks, 256, 0, s>>>(A, B, ncol, L, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
-  sum_col_partials<<<(ncol + 127) / 128, 128, 0, s>>>(partial, kGramBlocks, ncol, d);
+  warp_sum_partials<<<(ncol + 7) / 8, 256, 0, s>>>(partial, kColdotBlocks, kMaxCols, ncol, d);
   return cudaGetLastError();
 }
 
 __global__ void gather_cols_kernel(const double *__restrict__ X, int nv, const int *__restrict__ idx,
-                                   int n, long long L, double *__restrict__ Out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < L * n;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long a = e / n;
-    Out[e] = X[a * nv + idx[e - a * n]];
+                                   int n, long long L, double *__restrict__ Out, FastDiv fd) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < (uint32_t)(L * n);
+       e += gridDim.x * blockDim.x) {
+    const uint32_t a = fdiv(e, fd);
+    Out[e] = X[(size_t)a * nv + idx[e - a * (uint32_t)n]];
   }
 }
 
@@ -230,8 +259,13 @@ int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148
 
 }  // namespace
 
+template <typename T, typename TA>
+cudaError_t launch_stripe_gram(const T *A, int n1, const T *B, int n2, long long L, double *G,
+                               double *partial, cudaStream_t s);
+
 cudaError_t launch_gram(const double *A, int n1, const double *B, int n2, long long L, double *G,
                         double *partial, cudaStream_t s) {
+  if (n1 <= 64 && n2 <= 64) return launch_stripe_gram<double, double>(A, n1, B, n2, L, G, partial, s);
   return gram_t<double, double>(A, n1, B, n2, L, G, partial, s);
 }
 cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long long L,
@@ -282,7 +316,7 @@ cudaError_t launch_coldot_f32(const float *A, const float *B, int ncol, long lon
 cudaError_t launch_gather_cols(const double *X, int nv, const int *idx, int n, long long L,
                                double *Out, cudaStream_t s) {
   ::invdft::count_launch();
-  gather_cols_kernel<<<grid_for(L * n), 256, 0, s>>>(X, nv, idx, n, L, Out);
+  gather_cols_kernel<<<grid_for(L * n), 256, 0, s>>>(X, nv, idx, n, L, Out, make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_convert_f64_to_f32(const double *x, float *y, long long n, cudaStream_t s) {
@@ -298,6 +332,476 @@ cudaError_t launch_convert_f32_to_f64(const float *x, double *y, long long n, cu
 cudaError_t launch_fill_random(double *X, long long n, unsigned long long seed, cudaStream_t s) {
   ::invdft::count_launch();
   fill_normal<<<grid_for(n), 256, 0, s>>>(X, n, seed);
+  return cudaGetLastError();
+}
+
+}  // namespace invdft
+
+// ---------------------------------------------------------------------------
+// Tall-skinny FP32 kernels for the deflation of the MINRES blocks
+// (Z <- Z - Psi (Psi^T Z), n1, n2 <= 64).
+namespace invdft {
+namespace {
+
+constexpr int kTsRows = 32;       // rows per staged chunk
+constexpr int kTsLd = 68;         // padded row length in shared memory
+
+// partial[b][i][j] = sum over the rows of CTA b of A[a][i] B[a][j]; FP32
+// accumulation of a 4x4 tile per thread, chunks double-buffered in shared
+// memory with cp.async so that the next chunk loads while this one is used.
+__global__ void __launch_bounds__(256) ts_gram_f32(const float *__restrict__ A, int n1,
+                                                   const float *__restrict__ B, int n2,
+                                                   long long L, double *__restrict__ partial) {
+  __shared__ __align__(16) float sA[2][kTsRows][kTsLd];
+  __shared__ __align__(16) float sB[2][kTsRows][kTsLd];
+  const int tid = threadIdx.x;
+  const int ti = tid / 16, tj = tid % 16;
+  const long long rows_per = ((L + gridDim.x - 1) / gridDim.x + kTsRows - 1) / kTsRows * kTsRows;
+  const long long r_begin = blockIdx.x * rows_per;
+  const long long r_end = min(L, r_begin + rows_per);
+  float acc[4][4] = {};
+  auto stage = [&](int buf, long long r0) {
+    // rows r0..r0+31 of A and B (contiguous blocks), 4-byte cp.async
+    const int na = kTsRows * n1, nbb = kTsRows * n2;
+    for (int e = tid; e < na; e += 256) {
+      const int r = e / n1, c = e - r * n1;
+      float *dst = &sA[buf][r][c];
+      if (r0 + r < r_end) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(A + (r0 + r) * n1 + c));
+      } else {
+        *dst = 0.f;
+      }
+    }
+    for (int e = tid; e < nbb; e += 256) {
+      const int r = e / n2, c = e - r * n2;
+      float *dst = &sB[buf][r][c];
+      if (r0 + r < r_end) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(B + (r0 + r) * n2 + c));
+      } else {
+        *dst = 0.f;
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // zero the padding columns once (never written by the copies)
+  for (int e = tid; e < 2 * kTsRows; e += 256) {
+    const int buf = e / kTsRows, r = e % kTsRows;
+    for (int c = n1; c < kTsLd; ++c) sA[buf][r][c] = 0.f;
+    for (int c = n2; c < kTsLd; ++c) sB[buf][r][c] = 0.f;
+  }
+  __syncthreads();
+  int buf = 0;
+  if (r_begin < r_end) stage(0, r_begin);
+  for (long long r0 = r_begin; r0 < r_end; r0 += kTsRows) {
+    const bool more = r0 + kTsRows < r_end;
+    if (more) stage(buf ^ 1, r0 + kTsRows);
+    if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+#pragma unroll 8
+    for (int r = 0; r < kTsRows; ++r) {
+      const float4 a = *reinterpret_cast<const float4 *>(&sA[buf][r][ti * 4]);
+      const float4 b = *reinterpret_cast<const float4 *>(&sB[buf][r][tj * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  double *out = partial + (size_t)blockIdx.x * n1 * n2;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = ti * 4 + x, j = tj * 4 + y;
+      if (i < n1 && j < n2) out[i * n2 + j] = (double)acc[x][y];
+    }
+}
+
+__global__ void ts_sum_partials(const double *__restrict__ partial, int nblk, int n,
+                                double *__restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * n + e];
+  G[e] = s;
+}
+
+// Z[a][j] += sum_i Psi[a][i] Cf[i][j] with Cf = alpha * C in FP32; a CTA owns
+// 128 rows; warp w handles rows (w % 4) * 32 + lane and columns
+// [32 * (w / 4), +32) with 32 register accumulators.
+__global__ void __launch_bounds__(256) ts_rotate_f32(const float *__restrict__ Psi, int n1,
+                                                     const double *__restrict__ C, int n2,
+                                                     long long L, float *__restrict__ Z,
+                                                     double alpha) {
+  __shared__ float sC[64][64];
+  __shared__ float sP[128][65];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int i = e / 64, j = e % 64;
+    sC[i][j] = (i < n1 && j < n2) ? (float)(alpha * C[i * n2 + j]) : 0.f;
+  }
+  const int rloc = (warp & 3) * 32 + lane;
+  const int j0 = (warp >> 2) * 32;
+  for (long long a0 = (long long)blockIdx.x * 128; a0 < L; a0 += (long long)gridDim.x * 128) {
+    __syncthreads();
+    const int rows = (int)min((long long)128, L - a0);
+    for (int e = tid; e < 128 * n1; e += 256) {
+      const int r = e / n1, i = e - r * n1;
+      sP[r][i] = r < rows ? Psi[(a0 + r) * n1 + i] : 0.f;
+    }
+    __syncthreads();
+    if (j0 >= n2) continue;
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    for (int i = 0; i < n1; ++i) {
+      const float psi = sP[rloc][i];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = fmaf(psi, sC[i][j0 + j], acc[j]);
+    }
+    if (rloc < rows) {
+      float *zr = Z + (a0 + rloc) * n2;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j0 + j < n2) zr[j0 + j] += acc[j];
+    }
+  }
+}
+
+int ts_grid(long long L) { return (int)std::min<long long>((L + 127) / 128, 148LL * 8); }
+
+}  // namespace
+
+cudaError_t launch_deflate_gram_f32(const float *Psi, int n1, const float *Z, int n2, long long L,
+                                    double *G, double *partial, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
+  ::invdft::count_launch();
+  ts_gram_f32<<<kGramBlocks, 256, 0, s>>>(Psi, n1, Z, n2, L, partial);
+  ::invdft::count_launch();
+  ts_sum_partials<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, n1 * n2, G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deflate_update_f32(const float *Psi, int n1, const double *C, int n2,
+                                      long long L, float *Z, double alpha, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
+  ::invdft::count_launch();
+  ts_rotate_f32<<<ts_grid(L), 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace invdft
+
+// ---------------------------------------------------------------------------
+// Row-striped tall-skinny Gram for any n1, n2 <= 64: a thread owns a 4x4
+// output tile; when the n1 x n2 output has fewer tiles than the CTA has
+// threads, the spare threads split the rows of each staged chunk ("stripes")
+// and the stripes are summed in shared memory at the end.  T is the storage
+// type, TA the accumulator (FP32 for the MINRES deflation, FP64 otherwise).
+namespace invdft {
+namespace {
+
+constexpr int kSgRows = 32;
+
+template <typename T, typename TA>
+__global__ void __launch_bounds__(256) stripe_gram(const T *__restrict__ A, int n1,
+                                                   const T *__restrict__ B, int n2, long long L,
+                                                   double *__restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char sg_raw[];
+  T *sA = reinterpret_cast<T *>(sg_raw);                       // [2][kSgRows][n1]
+  T *sB = sA + 2 * kSgRows * n1;                               // [2][kSgRows][n2]
+  const int tid = threadIdx.x;
+  const int ntj = (n2 + 3) / 4, tiles = ((n1 + 3) / 4) * ntj;
+  const int S = max(1, 256 / tiles);
+  const int tile = tid % tiles, stripe = tid / tiles;
+  const bool active = stripe < S && tid < S * tiles;
+  const int i0 = (tile / ntj) * 4, j0 = (tile % ntj) * 4;
+  const long long rows_per = ((L + gridDim.x - 1) / gridDim.x + kSgRows - 1) / kSgRows * kSgRows;
+  const long long r_begin = blockIdx.x * rows_per;
+  const long long r_end = min(L, r_begin + rows_per);
+  TA acc[4][4] = {};
+  auto stage = [&](int buf, long long r0) {
+    const int rows = (int)min((long long)kSgRows, r_end - r0);
+    T *da = sA + buf * kSgRows * n1;
+    T *db = sB + buf * kSgRows * n2;
+    for (int e = tid; e < kSgRows * n1; e += 256) {
+      if (e < rows * n1) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(da + e)), "l"(A + r0 * n1 + e),
+                        "n"(sizeof(T)) : "memory");
+      } else {
+        da[e] = (T)0;
+      }
+    }
+    for (int e = tid; e < kSgRows * n2; e += 256) {
+      if (e < rows * n2) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(db + e)), "l"(B + r0 * n2 + e),
+                        "n"(sizeof(T)) : "memory");
+      } else {
+        db[e] = (T)0;
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int buf = 0;
+  if (r_begin < r_end) stage(0, r_begin);
+  for (long long r0 = r_begin; r0 < r_end; r0 += kSgRows) {
+    const bool more = r0 + kSgRows < r_end;
+    if (more) {
+      stage(buf ^ 1, r0 + kSgRows);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (active) {
+      const T *ra = sA + buf * kSgRows * n1;
+      const T *rb = sB + buf * kSgRows * n2;
+      for (int r = stripe; r < kSgRows; r += S) {
+        TA av[4], bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          av[x] = i0 + x < n1 ? (TA)ra[r * n1 + i0 + x] : (TA)0;
+          bv[x] = j0 + x < n2 ? (TA)rb[r * n2 + j0 + x] : (TA)0;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  // sum the stripes (reuse the staging area)
+  TA *red = reinterpret_cast<TA *>(sg_raw);                    // [S][tiles][16]
+  if (active)
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) red[((size_t)stripe * tiles + tile) * 16 + x * 4 + y] = acc[x][y];
+  __syncthreads();
+  double *out = partial + (size_t)blockIdx.x * n1 * n2;
+  for (int e = tid; e < tiles * 16; e += 256) {
+    const int tl = e / 16, xy = e % 16;
+    const int i = (tl / ntj) * 4 + xy / 4, j = (tl % ntj) * 4 + xy % 4;
+    if (i >= n1 || j >= n2) continue;
+    double s = 0.0;
+    for (int st = 0; st < S; ++st) s += (double)red[((size_t)st * tiles + tl) * 16 + xy];
+    out[i * n2 + j] = s;
+  }
+}
+
+// Z[a][j] += sum_i Psi[a][i] Cf[i][j]: a thread owns one row and NJ columns
+template <typename T, int NJ>
+__global__ void __launch_bounds__(256) stripe_rotate(const T *__restrict__ Psi, int n1,
+                                                     const double *__restrict__ C, int n2,
+                                                     long long L, T *__restrict__ Z,
+                                                     double alpha) {
+  extern __shared__ __align__(16) unsigned char sr_raw[];
+  const int ncg = (n2 + NJ - 1) / NJ;
+  const int rows_blk = 256 / ncg;
+  T *sC = reinterpret_cast<T *>(sr_raw);                       // [n1][ncg * NJ]
+  T *sP = sC + n1 * ncg * NJ;                                  // [rows_blk][n1 + 1]
+  const int tid = threadIdx.x;
+  const int ldc = ncg * NJ;
+  for (int e = tid; e < n1 * ldc; e += 256) {
+    const int i = e / ldc, j = e % ldc;
+    sC[e] = j < n2 ? (T)(alpha * C[i * n2 + j]) : (T)0;
+  }
+  const int cg = tid % ncg, r = tid / ncg;
+  const bool active = r < rows_blk;
+  for (long long a0 = (long long)blockIdx.x * rows_blk; a0 < L;
+       a0 += (long long)gridDim.x * rows_blk) {
+    __syncthreads();
+    const int rows = (int)min((long long)rows_blk, L - a0);
+    for (int e = tid; e < rows * n1; e += 256) {
+      const int rr = e / n1, i = e - rr * n1;
+      sP[rr * (n1 + 1) + i] = Psi[(a0 + rr) * n1 + i];
+    }
+    __syncthreads();
+    if (!active || r >= rows) continue;
+    T acc[NJ];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[j] = (T)0;
+    for (int i = 0; i < n1; ++i) {
+      const T psi = sP[r * (n1 + 1) + i];
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) acc[j] = fma(psi, sC[i * ldc + cg * NJ + j], acc[j]);
+    }
+    T *zr = Z + (a0 + r) * n2 + cg * NJ;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+      if (cg * NJ + j < n2) zr[j] += acc[j];
+  }
+}
+
+}  // namespace
+
+template <typename T, typename TA>
+cudaError_t launch_stripe_gram(const T *A, int n1, const T *B, int n2, long long L, double *G,
+                               double *partial, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
+  const int tiles = ((n1 + 3) / 4) * ((n2 + 3) / 4);
+  const int S = std::max(1, 256 / tiles);
+  const size_t stage = 2 * (size_t)kSgRows * (n1 + n2) * sizeof(T);
+  const size_t red = (size_t)S * tiles * 16 * sizeof(TA);
+  const size_t smem = std::max(stage, red);
+  cudaError_t e = cudaFuncSetAttribute(stripe_gram<T, TA>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
+  stripe_gram<T, TA><<<kGramBlocks, 256, smem, s>>>(A, n1, B, n2, L, partial);
+  ::invdft::count_launch();
+  warp_sum_partials<<<(n1 * n2 + 7) / 8, 256, 0, s>>>(partial, kGramBlocks, (size_t)n1 * n2,
+                                                      n1 * n2, G);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stripe_rotate(const T *Psi, int n1, const double *C, int n2, long long L, T *Z,
+                                 double alpha, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > 128 || n2 > 128) return cudaErrorInvalidValue;
+  auto run = [&](auto kern, int NJ) -> cudaError_t {
+    const int ncg = (n2 + NJ - 1) / NJ;
+    const int rows_blk = 256 / ncg;
+    const size_t smem = sizeof(T) * ((size_t)n1 * ncg * NJ + (size_t)rows_blk * (n1 + 1));
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<long long>((L + rows_blk - 1) / rows_blk, 148LL * 8);
+    ::invdft::count_launch();
+    kern<<<grid, 256, smem, s>>>(Psi, n1, C, n2, L, Z, alpha);
+    return cudaGetLastError();
+  };
+  if (n2 <= 8) return run(stripe_rotate<T, 8>, 8);
+  return run(stripe_rotate<T, 16>, 16);
+}
+
+template cudaError_t launch_stripe_gram<float, float>(const float *, int, const float *, int,
+                                                      long long, double *, double *, cudaStream_t);
+template cudaError_t launch_stripe_gram<double, double>(const double *, int, const double *, int,
+                                                        long long, double *, double *,
+                                                        cudaStream_t);
+template cudaError_t launch_stripe_rotate<float>(const float *, int, const double *, int,
+                                                 long long, float *, double, cudaStream_t);
+template cudaError_t launch_stripe_rotate<double>(const double *, int, const double *, int,
+                                                  long long, double *, double, cudaStream_t);
+
+}  // namespace invdft
+
+// ---------------------------------------------------------------------------
+// Register-tiled FP32 deflation update with an optional fused column dot:
+//   Z[a][j] += sum_i Psi[a][i] (alpha C)[i][j]         (n1, n2 <= 64)
+//   partial[b][j] = sum over the rows of CTA b of V[a][j] Z_new[a][j]
+// A thread owns 8 rows x 4 columns of a 128 x 64 tile; Psi rows are staged in
+// shared memory, C is resident.
+namespace invdft {
+namespace {
+
+template <bool DOT>
+__global__ void __launch_bounds__(256) defl_update_f32(const float *__restrict__ Psi, int n1,
+                                                       const double *__restrict__ C, int n2,
+                                                       long long L, float *__restrict__ Z,
+                                                       double alpha, const float *__restrict__ V,
+                                                       double *__restrict__ partial) {
+  __shared__ __align__(16) float sC[64][64];
+  __shared__ float sP[128 * 65];
+  __shared__ double red[16][64];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int ld = n1 + 1;
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int i = e / 64, j = e % 64;
+    sC[i][j] = (i < n1 && j < n2) ? (float)(alpha * C[i * n2 + j]) : 0.f;
+  }
+  double dsum[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long a0 = (long long)blockIdx.x * 128; a0 < L; a0 += (long long)gridDim.x * 128) {
+    __syncthreads();
+    const int rows = (int)min((long long)128, L - a0);
+    const float *src = Psi + a0 * n1;
+    for (int e = tid; e < rows * n1; e += 256) {
+      const int r = e / n1, i = e - r * n1;
+      sP[r * ld + i] = __ldg(src + e);
+    }
+    __syncthreads();
+    float acc[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
+    for (int i = 0; i < n1; ++i) {
+      const float4 c4 = *reinterpret_cast<const float4 *>(&sC[i][tx * 4]);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float pv = sP[(ty * 8 + r) * ld + i];
+        acc[r][0] = fmaf(pv, c4.x, acc[r][0]);
+        acc[r][1] = fmaf(pv, c4.y, acc[r][1]);
+        acc[r][2] = fmaf(pv, c4.z, acc[r][2]);
+        acc[r][3] = fmaf(pv, c4.w, acc[r][3]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int rr = ty * 8 + r;
+      if (rr >= rows) continue;
+      float *zr = Z + (a0 + rr) * n2;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int col = tx * 4 + q;
+        if (col < n2) {
+          const float z = zr[col] + acc[r][q];
+          zr[col] = z;
+          if (DOT) dsum[q] += (double)V[(a0 + rr) * n2 + col] * (double)z;
+        }
+      }
+    }
+  }
+  if (DOT) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[ty][tx * 4 + q] = dsum[q];
+    __syncthreads();
+    if (tid < n2) {
+      double s = 0.0;
+      for (int k = 0; k < 16; ++k) s += red[k][tid];
+      partial[(size_t)blockIdx.x * kMaxCols + tid] = s;
+    }
+  }
+}
+
+__global__ void warp_sum_cols(const double *__restrict__ partial, int nblk, int n,
+                              double *__restrict__ out) {
+  const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[(size_t)b * kMaxCols + e];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[e] = s;
+}
+
+}  // namespace
+
+cudaError_t launch_defl_update_f32(const float *Psi, int n1, const double *C, int n2, long long L,
+                                   float *Z, double alpha, const float *V, double *dot_out,
+                                   double *partial, cudaStream_t s) {
+  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>((L + 127) / 128, 148LL * 4);
+  ::invdft::count_launch();
+  if (V) {
+    defl_update_f32<true><<<grid, 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha, V, partial);
+    ::invdft::count_launch();
+    warp_sum_cols<<<(n2 + 7) / 8, 256, 0, s>>>(partial, grid, n2, dot_out);
+  } else {
+    defl_update_f32<false><<<grid, 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha, nullptr, nullptr);
+  }
   return cudaGetLastError();
 }
 

@@ -19,12 +19,12 @@ template <typename T>
 __global__ void hx_nodal(const T *__restrict__ X, T *__restrict__ Z, const double *__restrict__ v,
                          long long L, int ncol, double alpha, double shift,
                          const double *__restrict__ shift_col, const T *__restrict__ W, double beta,
-                         const float *__restrict__ E, const double *__restrict__ escale) {
-  const long long n = L * (long long)ncol;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long a = i / ncol;
-    const int j = (int)(i - a * ncol);
+                         const float *__restrict__ E, const double *__restrict__ escale,
+                         FastDiv fd) {
+  const uint32_t n = (uint32_t)(L * (long long)ncol);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t a = fdiv(i, fd);
+    const int j = (int)(i - a * (uint32_t)ncol);
     const double sh = shift_col ? shift_col[j] : shift;
     double z = alpha * (v[a] - sh) * (double)X[i];
     if (W) z += beta * (double)W[i];
@@ -186,7 +186,7 @@ cudaError_t launch_hx_t(const Geom &g, const double *v, const HxArgs<T> &a, cuda
   int blocks = (int)std::min<long long>((n + 255) / 256, 148LL * 16);
   ::invdft::count_launch();
   hx_nodal<T><<<blocks, 256, 0, s>>>(a.X, a.Z, v, g.L, a.ncol, a.alpha, a.shift, a.shift_col, a.W,
-                                     a.beta, a.E, a.escale);
+                                     a.beta, a.E, a.escale, make_fastdiv(a.ncol));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const double scale = a.alpha * g.kc;
@@ -219,6 +219,8 @@ cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
   const bool tc = a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
                   (const void *)a.Z != (const void *)a.E;
   if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + 8, s);
+  const bool simt_q4 = c->g.p == 4 && c->cell_perm && !a.E && a.Z != a.X && a.Z != a.W;
+  if (simt_q4) return launch_hx_simt_q4(c->g, c->v, a, c->cell_perm, s);
   return launch_hx(c->g, c->v, a, s);
 }
 

@@ -142,6 +142,26 @@ void count_launch();
     if (!::invdft::cuda_ok((c), cudaGetLastError(), what)) return INVDFT_ECUDA; \
   } while (0)
 
+// Division by a runtime constant for 32-bit indices x < 2^31 (Granlund &
+// Montgomery 1994): q = (umulhi(x, m) + x) >> s with s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  uint32_t d = 1, m = 1, s = 0;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.s = 0;
+  while ((1ull << f.s) < d) ++f.s;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << f.s) - d)) / d + 1);
+  return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv &f) {
+  return (__umulhi(x, f.m) + x) >> f.s;
+}
+#endif
+
 // ------------------------------------------------------------ H~X (hx.cu)
 // Z = alpha * (H~ X - shift o X) + beta * W + alpha * E diag(escale)
 //   shift: per-column (shift_col != nullptr) or the scalar shift;
@@ -172,6 +192,8 @@ size_t tc_cell_matrix_floats();
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
                          const int *perm, int *err, cudaStream_t s);
 void build_cell_order(int nc, std::vector<int> *perm);
+cudaError_t launch_hx_simt_q4(const Geom &g, const double *v, const HxArgs<float> &a,
+                              const int *perm, cudaStream_t s);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).
@@ -182,6 +204,25 @@ cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long
 // FP32 inputs, FP32 accumulation inside a CTA, FP64 across CTAs
 cudaError_t launch_gram_f32acc(const float *A, int n1, const float *B, int n2, long long L,
                                double *G, double *partial, cudaStream_t s);
+// FP32 tall-skinny pair for the deflation of MINRES blocks (n1, n2 <= 64):
+// G = Psi^T Z (FP32 within a CTA, FP64 across CTAs) and Z += alpha Psi C
+cudaError_t launch_deflate_gram_f32(const float *Psi, int n1, const float *Z, int n2, long long L,
+                                    double *G, double *partial, cudaStream_t s);
+cudaError_t launch_deflate_update_f32(const float *Psi, int n1, const double *C, int n2,
+                                      long long L, float *Z, double alpha, cudaStream_t s);
+// Row-striped tall-skinny Gram (n1, n2 <= 64) and row-tiled update
+// (n1, n2 <= 128): G = A^T B, Z += alpha Psi C
+template <typename T, typename TA>
+cudaError_t launch_stripe_gram(const T *A, int n1, const T *B, int n2, long long L, double *G,
+                               double *partial, cudaStream_t s);
+template <typename T>
+cudaError_t launch_stripe_rotate(const T *Psi, int n1, const double *C, int n2, long long L, T *Z,
+                                 double alpha, cudaStream_t s);
+// Register-tiled FP32 update Z += alpha Psi C (n1, n2 <= 64); with V != null
+// also dot_out[j] = sum_a V[a][j] Z_new[a][j] (FP64 accumulation)
+cudaError_t launch_defl_update_f32(const float *Psi, int n1, const double *C, int n2, long long L,
+                                   float *Z, double alpha, const float *V, double *dot_out,
+                                   double *partial, cudaStream_t s);
 // Xo += alpha * Xi Cm  (n1 -> n2 columns) in the storage precision T
 template <typename T>
 cudaError_t launch_rotate_acc(const T *Xi, int n1, const double *Cm, int n2, long long L, T *Xo,

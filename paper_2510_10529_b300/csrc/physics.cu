@@ -9,11 +9,15 @@
 namespace invdft {
 namespace {
 
-int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
+int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 8); }
 
 #define GRID_STRIDE(i, n)                                                          \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
        i += (long long)gridDim.x * blockDim.x)
+// 32-bit grid stride over an [L][n] block (L * n < 2^31 is checked at handle creation)
+#define GRID_STRIDE32(i, total)                                                         \
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < (uint32_t)(total);       \
+       i += gridDim.x * blockDim.x)
 
 __global__ void density_kernel(const double *__restrict__ X, int n, const double *__restrict__ occ,
                                const double *__restrict__ mass, long long L,
@@ -76,10 +80,10 @@ __global__ void adjoint_rhs_kernel(const double *__restrict__ X, int nv, const i
                                    const double *__restrict__ dLdrho,
                                    const double *__restrict__ mass, long long L,
                                    double *__restrict__ Psi_o, double *__restrict__ R,
-                                   double *__restrict__ Wo) {
-  GRID_STRIDE(e, L * no) {
-    const long long a = e / no;
-    const int c = (int)(e - a * no);
+                                   double *__restrict__ Wo, FastDiv fd) {
+  GRID_STRIDE32(e, L * no) {
+    const uint32_t a = fdiv(e, fd);
+    const int c = (int)(e - a * (uint32_t)no);
     const double psi = X[a * nv + idx[c]];
     const double omega = -dLdrho[a] / (2.0 * mass[a]);
     Psi_o[e] = psi;
@@ -189,9 +193,10 @@ __global__ void lincomb_kernel(double a, const double *__restrict__ x, double b,
 
 __global__ void residual_block_kernel(const double *__restrict__ HX, const double *__restrict__ X,
                                       const double *__restrict__ theta, int n, long long L,
-                                      double *__restrict__ E64, float *__restrict__ E32) {
-  GRID_STRIDE(e, L * n) {
-    const int j = (int)(e % n);
+                                      double *__restrict__ E64, float *__restrict__ E32,
+                                      FastDiv fd) {
+  GRID_STRIDE32(e, L * n) {
+    const int j = (int)(e - fdiv(e, fd) * (uint32_t)n);
     const double r = HX[e] - theta[j] * X[e];
     if (E64) E64[e] = r;
     if (E32) E32[e] = (float)r;
@@ -200,9 +205,9 @@ __global__ void residual_block_kernel(const double *__restrict__ HX, const doubl
 
 __global__ void cheb_combine_kernel(const double *__restrict__ X, const double *__restrict__ pm,
                                     const float *__restrict__ D, int n, long long L,
-                                    double *__restrict__ Y) {
-  GRID_STRIDE(e, L * n) {
-    const int j = (int)(e % n);
+                                    double *__restrict__ Y, FastDiv fd) {
+  GRID_STRIDE32(e, L * n) {
+    const int j = (int)(e - fdiv(e, fd) * (uint32_t)n);
     Y[e] = X[e] * pm[j] + (double)D[e];
   }
 }
@@ -216,13 +221,20 @@ template <typename T>
 __global__ void mr_lanczos_kernel(const T *__restrict__ p, const T *__restrict__ q,
                                   const T *__restrict__ qprev, const double *__restrict__ alpha,
                                   const double *__restrict__ beta, const double *__restrict__ prec,
-                                  int n, long long L, T *__restrict__ qhat, T *__restrict__ zhat) {
-  GRID_STRIDE(e, L * n) {
-    const long long a = e / n;
-    const int c = (int)(e - a * n);
-    const double r = (double)p[e] - alpha[c] * (double)q[e] - beta[c] * (double)qprev[e];
-    qhat[e] = (T)r;
-    zhat[e] = (T)(prec[a] * r);
+                                  int n, long long L, T *__restrict__ qhat, T *__restrict__ zhat,
+                                  FastDiv fd) {
+  __shared__ T sa[kMaxCols], sb[kMaxCols];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    sa[c] = (T)alpha[c];
+    sb[c] = (T)beta[c];
+  }
+  __syncthreads();
+  GRID_STRIDE32(e, L * n) {
+    const uint32_t a = fdiv(e, fd);
+    const int c = (int)(e - a * (uint32_t)n);
+    const T r = p[e] - sa[c] * q[e] - sb[c] * qprev[e];
+    qhat[e] = r;
+    zhat[e] = (T)prec[a] * r;
   }
 }
 
@@ -275,50 +287,60 @@ __global__ void mr_update_kernel(T *__restrict__ z, const T *__restrict__ zhat,
                                  T *__restrict__ qn, const T *__restrict__ qhat,
                                  T *__restrict__ wpp, const T *__restrict__ wp,
                                  T *__restrict__ x, const double *__restrict__ st, int n,
-                                 long long L) {
-  const double *ceps = st + 10 * n, *cdel = st + 11 * n, *cig = st + 12 * n, *ct = st + 13 * n;
-  const double *cib = st + 14 * n;
-  GRID_STRIDE(e, L * n) {
-    const int c = (int)(e % n);
-    const double w = ((double)z[e] - ceps[c] * (double)wpp[e] - cdel[c] * (double)wp[e]) * cig[c];
-    wpp[e] = (T)w;
-    x[e] = (T)((double)x[e] + ct[c] * w);
-    qn[e] = (T)((double)qhat[e] * cib[c]);
-    z[e] = (T)((double)zhat[e] * cib[c]);
+                                 long long L, FastDiv fd) {
+  __shared__ T se[kMaxCols], sd[kMaxCols], sg[kMaxCols], st_[kMaxCols], sib[kMaxCols];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    se[c] = (T)st[10 * n + c];
+    sd[c] = (T)st[11 * n + c];
+    sg[c] = (T)st[12 * n + c];
+    st_[c] = (T)st[13 * n + c];
+    sib[c] = (T)st[14 * n + c];
+  }
+  __syncthreads();
+  GRID_STRIDE32(e, L * n) {
+    const int c = (int)(e - fdiv(e, fd) * (uint32_t)n);
+    const T w = (z[e] - se[c] * wpp[e] - sd[c] * wp[e]) * sg[c];
+    wpp[e] = w;
+    x[e] = x[e] + st_[c] * w;
+    qn[e] = qhat[e] * sib[c];
+    z[e] = zhat[e] * sib[c];
   }
 }
 
 template <typename T>
 __global__ void mr_init_kernel(const T *__restrict__ b, const T *__restrict__ zb,
                                const double *__restrict__ beta1, int n, long long L,
-                               T *__restrict__ q, T *__restrict__ z) {
-  GRID_STRIDE(e, L * n) {
-    const int c = (int)(e % n);
-    const double ib = beta1[c] > 0.0 ? 1.0 / beta1[c] : 0.0;
-    q[e] = (T)((double)b[e] * ib);
-    z[e] = (T)((double)zb[e] * ib);
+                               T *__restrict__ q, T *__restrict__ z, FastDiv fd) {
+  __shared__ T sib[kMaxCols];
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    sib[c] = beta1[c] > 0.0 ? (T)(1.0 / beta1[c]) : (T)0;
+  __syncthreads();
+  GRID_STRIDE32(e, L * n) {
+    const int c = (int)(e - fdiv(e, fd) * (uint32_t)n);
+    q[e] = b[e] * sib[c];
+    z[e] = zb[e] * sib[c];
   }
 }
 
 template <typename T>
 __global__ void prec_apply_kernel(const T *__restrict__ r, const double *__restrict__ prec, int n,
-                                  long long L, T *__restrict__ z) {
-  GRID_STRIDE(e, L * n) z[e] = (T)(prec[e / n] * (double)r[e]);
+                                  long long L, T *__restrict__ z, FastDiv fd) {
+  GRID_STRIDE32(e, L * n) z[e] = (T)prec[fdiv(e, fd)] * r[e];
 }
 
 __global__ void scatter_cols_kernel(const double *__restrict__ Po, int no,
                                     const int *__restrict__ idx, double *__restrict__ P, int nv,
-                                    long long L) {
-  GRID_STRIDE(e, L * no) {
-    const long long a = e / no;
-    const int c = (int)(e - a * no);
-    P[a * nv + idx[c]] = Po[e];
+                                    long long L, FastDiv fd) {
+  GRID_STRIDE32(e, L * no) {
+    const uint32_t a = fdiv(e, fd);
+    const int c = (int)(e - a * (uint32_t)no);
+    P[(size_t)a * nv + idx[c]] = Po[e];
   }
 }
 
 template <typename TI, typename TO>
 __global__ void add_convert_kernel(const TI *__restrict__ d, TO *__restrict__ p, long long n) {
-  GRID_STRIDE(i, n) p[i] = (TO)((double)p[i] + (double)d[i]);
+  GRID_STRIDE32(i, n) p[i] = p[i] + (TO)d[i];
 }
 
 }  // namespace
@@ -345,7 +367,7 @@ cudaError_t launch_adjoint_rhs(const double *X, int nv, const int *idx, int no, 
                                double *Psi_o, double *R, double *Wo, cudaStream_t s) {
   ::invdft::count_launch();
   adjoint_rhs_kernel<<<grid_for(L * no), 256, 0, s>>>(X, nv, idx, no, f_o, dLdrho, mass, L, Psi_o,
-                                                      R, Wo);
+                                                      R, Wo, make_fastdiv(no));
   return cudaGetLastError();
 }
 
@@ -429,13 +451,14 @@ cudaError_t launch_lincomb(double a, const double *x, double b, const double *y,
 cudaError_t launch_residual_block(const double *HX, const double *X, const double *theta, int n,
                                   long long L, double *E64, float *E32, cudaStream_t s) {
   ::invdft::count_launch();
-  residual_block_kernel<<<grid_for(L * n), 256, 0, s>>>(HX, X, theta, n, L, E64, E32);
+  residual_block_kernel<<<grid_for(L * n), 256, 0, s>>>(HX, X, theta, n, L, E64, E32,
+                                                        make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_cheb_combine(const double *X, const double *pm, const float *D, int n,
                                 long long L, double *Y, cudaStream_t s) {
   ::invdft::count_launch();
-  cheb_combine_kernel<<<grid_for(L * n), 256, 0, s>>>(X, pm, D, n, L, Y);
+  cheb_combine_kernel<<<grid_for(L * n), 256, 0, s>>>(X, pm, D, n, L, Y, make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_scale_f32(const float *E, const double *, double alpha, int n, long long L,
@@ -451,14 +474,15 @@ cudaError_t launch_mr_lanczos(const T *p, const T *q, const T *qprev, const doub
                               T *zhat, cudaStream_t s) {
   ::invdft::count_launch();
   mr_lanczos_kernel<T><<<grid_for(L * n), 256, 0, s>>>(p, q, qprev, alpha, beta, prec, n, L, qhat,
-                                                       zhat);
+                                                       zhat, make_fastdiv(n));
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_mr_update(T *z, const T *zhat, T *qn, const T *qhat, T *wpp, const T *wp, T *x,
                              const double *st, int n, long long L, cudaStream_t s) {
   ::invdft::count_launch();
-  mr_update_kernel<T><<<grid_for(L * n), 256, 0, s>>>(z, zhat, qn, qhat, wpp, wp, x, st, n, L);
+  mr_update_kernel<T><<<grid_for(L * n), 256, 0, s>>>(z, zhat, qn, qhat, wpp, wp, x, st, n, L,
+                                                      make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_mr_givens(int n, double *st, cudaStream_t s) {
@@ -470,20 +494,20 @@ template <typename T>
 cudaError_t launch_mr_init(const T *b, const T *zb, const double *beta1, int n, long long L, T *q,
                            T *z, cudaStream_t s) {
   ::invdft::count_launch();
-  mr_init_kernel<T><<<grid_for(L * n), 256, 0, s>>>(b, zb, beta1, n, L, q, z);
+  mr_init_kernel<T><<<grid_for(L * n), 256, 0, s>>>(b, zb, beta1, n, L, q, z, make_fastdiv(n));
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_prec_apply(const T *r, const double *prec, int n, long long L, T *z,
                               cudaStream_t s) {
   ::invdft::count_launch();
-  prec_apply_kernel<T><<<grid_for(L * n), 256, 0, s>>>(r, prec, n, L, z);
+  prec_apply_kernel<T><<<grid_for(L * n), 256, 0, s>>>(r, prec, n, L, z, make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_scatter_cols(const double *Po, int no, const int *idx, double *P, int nv,
                                 long long L, cudaStream_t s) {
   ::invdft::count_launch();
-  scatter_cols_kernel<<<grid_for(L * no), 256, 0, s>>>(Po, no, idx, P, nv, L);
+  scatter_cols_kernel<<<grid_for(L * no), 256, 0, s>>>(Po, no, idx, P, nv, L, make_fastdiv(no));
   return cudaGetLastError();
 }
 template <typename TI, typename TO>

@@ -184,11 +184,17 @@ double adj_tolerance(const Ctx *c) {
   return std::min(0.1, std::max(c->err_l2 * c->err_l2 / c->o.c_ad, 1e-10));
 }
 
-// States whose residual the forward solve drives to the tolerance, and states
-// that get an adjoint column.  With smearing, states of occupation below the
-// cut (1e-8) change the gradient by about that fraction of its norm.
+// Convergence weight of a state in the forward solve: with smearing, a state
+// of occupation f changes the density in proportion to f, so its residual is
+// weighted by min(1, f / 1e-4); states below f = 1e-8 are ignored.  (The
+// highest Ritz vectors of the block converge slowest and, near a dense Fermi
+// level, still carry small occupations.)
+double conv_weight(const Ctx *c, double f) {
+  if (c->o.kT <= 0) return f > 0.0 ? 1.0 : 0.0;
+  if (!(f > 1e-8)) return 0.0;
+  return std::min(1.0, f / 1e-4);
+}
 bool state_active(const Ctx *c, double f) { return c->o.kT > 0 ? f > 1e-8 : f > 0.0; }
-bool adjoint_active(const Ctx *c, double f) { return state_active(c, f); }
 
 }  // namespace
 
@@ -336,7 +342,7 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
     }
     maxres = 0.0;
     for (int i = 0; i < n; ++i)
-      if (state_active(c, occ[i])) maxres = std::max(maxres, std::sqrt(std::max(res2[i], 0.0)));
+      maxres = std::max(maxres, conv_weight(c, occ[i]) * std::sqrt(std::max(res2[i], 0.0)));
     if (maxres <= tol && pass >= 1) break;
     if (pass >= c->o.max_cheb_passes) {
       status = INVDFT_ENOCONV;
@@ -384,18 +390,47 @@ struct AdjPlan {
   double *d_eps_o = nullptr, *d_f_o = nullptr;
 };
 
-// Z <- Z - Psi (Psi^T Z): projection onto the complement of the nv computed
-// Ritz vectors (Psi [L][nv], Z [L][no], both in precision T).
+// Z <- Z - Psi (Psi^T Z): projection onto the complement of the deflation
+// vectors (Psi [L][nv], Z [L][no], both in precision T).  With V != null the
+// FP32 path also returns dot[j] = V_j . Z_j (after the projection) from the
+// same pass.
 template <typename T>
-invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s) {
+invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s,
+                      const T *V = nullptr, double *dot = nullptr) {
   double *Cp = c->small + 4 * kMaxGram * kMaxGram;
-  if (sizeof(T) == 8)
-    CU(launch_gram((const double *)Psi, nv, (const double *)Z, no, c->L, Cp, c->partial, s),
-       "gram(deflate)");
-  else
+  const bool big = ((nv + 3) / 4) * ((no + 3) / 4) >= 128;
+  if (sizeof(T) == 8) {
+    if (nv <= 64 && no <= 64)
+      CU((launch_stripe_gram<double, double>((const double *)Psi, nv, (const double *)Z, no, c->L,
+                                             Cp, c->partial, s)), "gram(deflate)");
+    else
+      CU(launch_gram((const double *)Psi, nv, (const double *)Z, no, c->L, Cp, c->partial, s),
+         "gram(deflate)");
+    CU(launch_stripe_rotate<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "update(deflate)");
+    if (V) CU(launch_coldot((const double *)V, (const double *)Z, no, c->L, dot, c->partial, s), "coldot");
+    return INVDFT_OK;
+  }
+  if (nv > 64 || no > 64) {
     CU(launch_gram_f32acc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
        "gram(deflate)");
-  CU(launch_rotate_acc<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "rotate(deflate)");
+    CU(launch_rotate_acc<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "rotate(deflate)");
+    if (V) CU(launch_coldot_f32((const float *)V, (const float *)Z, no, c->L, dot, c->partial, s), "coldot");
+    return INVDFT_OK;
+  }
+  if (big)
+    CU(launch_deflate_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial,
+                               s), "gram(deflate)");
+  else
+    CU((launch_stripe_gram<float, float>((const float *)Psi, nv, (const float *)Z, no, c->L, Cp,
+                                         c->partial, s)), "gram(deflate)");
+  if (no >= 32) {
+    CU(launch_defl_update_f32((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
+                              (const float *)V, dot, c->partial, s), "update(deflate)");
+  } else {
+    // narrow blocks: one row per thread keeps every thread busy
+    CU(launch_stripe_rotate<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "update(deflate)");
+    if (V) CU(launch_coldot_f32((const float *)V, (const float *)Z, no, c->L, dot, c->partial, s), "coldot");
+  }
   return INVDFT_OK;
 }
 
@@ -446,24 +481,21 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, cons
       if (!any) break;
     }
     HxArgs<T> a;
-    set_tc(a, c->o.prec == INVDFT_MIXED);
+    // the inner MINRES operator stays on the FP32 CUDA cores: with TF32
+    // operands (relative error ~3e-4) the inner solves stall early and the
+    // FP64 refinement needs several times more outer passes
+    set_tc(a, false);
     a.X = z;
     a.Z = p;
     a.ncol = n;
     a.shift_col = pl.d_eps_o;
     CU(hx_op(c, a, s), "hx(minres)");
-    TRY(deflate<T>(c, Psi, nv, p, n, s));
-    if (sizeof(T) == 8)
-      CU(launch_coldot((const double *)z, (const double *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
-    else
-      CU(launch_coldot_f32((const float *)z, (const float *)p, n, L, st + kMrAlpha * n, c->partial, s), "coldot");
+    // p <- Q p, alpha = z . p
+    TRY(deflate<T>(c, Psi, nv, p, n, s, z, st + kMrAlpha * n));
     CU(launch_mr_lanczos<T>(p, q, qprev, st + kMrAlpha * n, st + kMrBeta * n, c->prec_diag, n, L,
                             p, zh, s), "mr_lanczos");
-    TRY(deflate<T>(c, Psi, nv, zh, n, s));
-    if (sizeof(T) == 8)
-      CU(launch_coldot((const double *)p, (const double *)zh, n, L, st + kMrBnext * n, c->partial, s), "coldot");
-    else
-      CU(launch_coldot_f32((const float *)p, (const float *)zh, n, L, st + kMrBnext * n, c->partial, s), "coldot");
+    // zhat <- Q zhat, beta_next^2 = qhat . zhat
+    TRY(deflate<T>(c, Psi, nv, zh, n, s, p, st + kMrBnext * n));
     CU(launch_mr_givens(n, st, s), "mr_givens");
     CU(launch_mr_update<T>(z, zh, qprev, p, wpp, wp, x, st, n, L, s), "mr_update");
     std::swap(qprev, q);
@@ -505,9 +537,16 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   TRY(fetch(c, c->eps, nv * sizeof(double), eps.data(), s));
   TRY(fetch(c, c->occ, nv * sizeof(double), f.data(), s));
   TRY(fetch(c, c->dfde, nv * sizeof(double), dfde.data(), s));
+  // adjoint columns: occupied states that are converged (residual <= 10
+  // t_eig) or carry f >= 1e-4 (those are converged by the weighted test)
+  std::vector<double> res2(nv);
+  TRY(fetch(c, c->scal + kScRes, nv * sizeof(double), res2.data(), s));
+  const double rtol = 10.0 * std::max(c->eig_tol_used, 1e-12);
+  auto converged = [&](int i) { return std::sqrt(std::max(res2[i], 0.0)) <= rtol; };
   AdjPlan pl;
   for (int i = 0; i < nv; ++i)
-    if (adjoint_active(c, f[i])) pl.idx.push_back(i);
+    if (state_active(c, f[i]) && (converged(i) || conv_weight(c, f[i]) >= 1.0))
+      pl.idx.push_back(i);
   pl.no = (int)pl.idx.size();
   const int no = pl.no;
   if (no == 0) {
@@ -524,12 +563,15 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   // deflation set: the active states and every other Ritz pair converged to
   // the eigen tolerance (an unconverged vector would carry its residual into
   // every column through the exact-ratio formula)
-  std::vector<double> res2(nv);
-  TRY(fetch(c, c->scal + kScRes, nv * sizeof(double), res2.data(), s));
   std::vector<int> dset;
-  const double rtol = 10.0 * std::max(c->eig_tol_used, 1e-12);
-  for (int i = 0; i < nv; ++i)
-    if (adjoint_active(c, f[i]) || std::sqrt(std::max(res2[i], 0.0)) <= rtol) dset.push_back(i);
+  {
+    size_t k = 0;
+    for (int i = 0; i < nv; ++i) {
+      const bool col = k < pl.idx.size() && pl.idx[k] == i;
+      if (col) ++k;
+      if (col || converged(i)) dset.push_back(i);
+    }
+  }
   const int nd = (int)dset.size();
   int *ibase = reinterpret_cast<int *>(c->scal + kScInt);
   pl.d_idx = ibase;
@@ -602,15 +644,21 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   int total_iters = 0, outer = 0;
   double relmax = 0.0;
   invdft_status status = INVDFT_OK;
+  // block-normwise criterion: |r_c| <= t_ad max_k |g~_k|, so that every column
+  // is accurate in proportion to its share of the gradient (columns of weakly
+  // occupied states have small right-hand sides)
+  double gmax = 0.0;
+  for (int k = 0; k < no; ++k) gmax = std::max(gmax, gn[k]);
   for (;; ++outer) {
     CU(launch_coldot(r64, r64, no, L, c->scal + kScCol, c->partial, s), "coldot");
     TRY(fetch(c, c->scal + kScCol, no * sizeof(double), rn.data(), s));
     relmax = 0.0;
     for (int k = 0; k < no; ++k) {
       const double r = std::sqrt(std::max(rn[k], 0.0));
-      const double rel = gn[k] > 0 ? r / gn[k] : 0.0;
+      const double rel = gmax > 0 ? r / gmax : 0.0;
       relmax = std::max(relmax, rel);
       const double floor_tol = mixed ? 1e-6 : 1e-14;
+      // inner tolerance relative to this column's current residual
       tol[k] = rel > tad ? std::max(floor_tol, std::min(0.5, 0.5 * tad / rel)) : 1.0;
     }
     if (relmax <= tad) break;
