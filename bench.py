@@ -28,6 +28,7 @@ workload (rank 0 only).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -49,8 +50,8 @@ METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 # H~X column-applications per inverse iteration on each workload, as counted by
 # the GPU path (line-search solves, Chebyshev passes, MINRES iterations) over the
 # timed steps of a mixed-precision run (cube32_q4_e100: 32,829 on average over
-# three steps; the others from the same count on their own workloads).  The
-# reference arm uses these fixed counts so that it never touches the GPU.
+# three steps; the smaller workloads carry estimates from their Chebyshev
+# pass and MINRES iteration counts).  The reference arm uses these fixed counts so that it never touches the GPU.
 COL_APPLIES_PER_STEP = {"cube32_q4_e100": 32829,
                         "cube24_q4_e20": 16 * 31 * 3 + 10 * 200,
                         "cube8_q2_he": 8 * 21 * 3 + 100, "cube32_q4_hx": 64}
@@ -66,6 +67,12 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-hx", action="store_true", help="skip the operator benchmark")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ncell", type=int, default=None,
+                    help="run the workload on NCELL^3 cells of the same box (a smaller case "
+                         "for kernel profiles; the printed line then names that mesh)")
+    ap.add_argument("--hx-case", nargs=3, metavar=("NCELL", "NCOL", "KIND"), default=None,
+                    help="only apply H~X three times on an NCELL^3 Q4 mesh with NCOL random "
+                         "columns, KIND tf32|fp32|fp64 (a small case for kernel profiles)")
     return ap.parse_args()
 
 
@@ -170,16 +177,17 @@ def hx_benchmark(device, reps32=20, reps64=3):
     out = {}
     ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
     flops = 2.0 * ne * ne * 64 * cells
-    for name, X, reps in (("mixed", X64.float(), reps32), ("fp64", X64, reps64)):
+    for name, X, reps, tc in (("mixed", X64.float(), reps32, True),
+                              ("fp32", X64.float(), reps32, False), ("fp64", X64, reps64, False)):
         Y = torch.empty_like(X)
         for _ in range(3):
-            P.invdft_apply_h(pb.h, X, Y)
+            P.invdft_apply_h(pb.h, X, Y, tc)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(reps):
-            P.invdft_apply_h(pb.h, X, Y)
+            P.invdft_apply_h(pb.h, X, Y, tc)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
@@ -187,6 +195,28 @@ def hx_benchmark(device, reps32=20, reps64=3):
         out[name] = {"ms": ms, "tflops_nominal": flops / ms / 1e9, "gbs": byt / ms / 1e6}
     pb.close()
     return {"workload": "cube32_q4_hx", "ncol": 64, "nominal_flops": flops, **out}
+
+
+def hx_case(ncell, ncol, kind, device):
+    """Three H~X applications on an ncell^3 Q4 mesh of the operator-benchmark box
+    (a small case that a kernel profiler can capture in seconds)."""
+    import torch
+
+    import paper_2510_10529_b300 as P
+    wl = W.cube32_q4_hx()
+    pb = P.Problem(wl.lo, wl.hi, ncell, 4, nstates=8, device=device)
+    xyz = pb.coords()
+    v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
+    pb.set_potential(torch.as_tensor(v, dtype=torch.float64, device=device))
+    X = torch.as_tensor(W.random_block(pb.L, ncol, wl.seed), device=device)
+    if kind != "fp64":
+        X = X.float()
+    Y = torch.empty_like(X)
+    for _ in range(3):
+        P.invdft_apply_h(pb.h, X, Y, kind == "tf32")
+    torch.cuda.synchronize()
+    pb.close()
+    print(json.dumps({"hx_case": {"ncell": ncell, "unknowns": pb.L, "ncol": ncol, "kind": kind}}))
 
 
 # ------------------------------------------------------------------ oracle baseline
@@ -223,6 +253,13 @@ def oracle_baseline(wl, col_applies_per_step: float, budget_s: float = 12.0):
 
 # ------------------------------------------------------------------ arms
 
+def workload_of(args):
+    wl = W.WORKLOADS[args.workload]()
+    if args.ncell:
+        wl = dataclasses.replace(wl, ncell=args.ncell)
+    return wl
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -233,7 +270,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(device)
     if world > 1:
         dist.init_process_group("nccl", device_id=device)
-    wl = W.WORKLOADS[args.workload]()
+    wl = workload_of(args)
     pb, d = build_problem(wl, args.prec, device)
     v_xc = torch.zeros(pb.L, dtype=torch.float64, device=device)
     rd, w = d["rho_data"], d["w"]
@@ -362,6 +399,12 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    if args.hx_case:
+        n, k, kind = args.hx_case
+        if kind not in ("tf32", "fp32", "fp64"):
+            raise SystemExit("--hx-case KIND must be tf32, fp32 or fp64")
+        hx_case(int(n), int(k), kind, "cuda")
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -33,7 +33,8 @@ namespace {
 
 __global__ void init_fields(const double *__restrict__ m1, const double *__restrict__ kA,
                             const double *__restrict__ kB, int Ni, double *__restrict__ mass,
-                            double *__restrict__ dvec, double *__restrict__ prec) {
+                            double *__restrict__ dvec, double *__restrict__ prec,
+                            float *__restrict__ precf) {
   const long long L = (long long)Ni * Ni * Ni;
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < L;
        a += (long long)gridDim.x * blockDim.x) {
@@ -44,14 +45,18 @@ __global__ void init_fields(const double *__restrict__ m1, const double *__restr
     mass[a] = m;
     dvec[a] = 1.0 / sqrt(m);
     prec[a] = m / kaa;          // inverse diagonal of D K D (Laplacian part)
+    precf[a] = (float)(m / kaa);
   }
 }
 
 __global__ void add_fields(const double *__restrict__ a, const double *__restrict__ b,
-                           double *__restrict__ out, long long n) {
+                           double *__restrict__ out, float *__restrict__ outf, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = a[i] + (b ? b[i] : 0.0);
+       i += (long long)gridDim.x * blockDim.x) {
+    const double x = a[i] + (b ? b[i] : 0.0);
+    out[i] = x;
+    outf[i] = (float)x;
+  }
 }
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 148LL * 16); }
@@ -72,9 +77,11 @@ size_t plan(Ctx *c, char *base) {
   c->mass = ar.take<double>(L);
   c->dvec = ar.take<double>(L);
   c->prec_diag = ar.take<double>(L);
+  c->precf = ar.take<float>(L);
   c->Ke_tc = ar.take<float>(tc_cell_matrix_floats());
   c->cell_perm = ar.take<int>((size_t)c->g.ncell * c->g.ncell * c->g.ncell);
   c->v = ar.take<double>(L);
+  c->vf = ar.take<float>(L);
   c->vfixed = ar.take<double>(L);
   c->rho = ar.take<double>(L);
   c->grad = ar.take<double>(L);
@@ -87,11 +94,14 @@ size_t plan(Ctx *c, char *base) {
   c->HY = ar.take<double>(blk);
   c->P = ar.take<double>(blk);
   c->Rg = ar.take<double>(blk);
-  c->C0 = ar.take<double>(blk);
+  // C0 and the MINRES buffers also hold FP32 blocks padded to a multiple of 4
+  // columns (at most 2 nv floats per node once nv >= 2)
+  const size_t blk2 = (size_t)L * std::max(nv, 2);
+  c->C0 = ar.take<double>(blk2);
   c->C1 = ar.take<double>(blk);
   c->C2 = ar.take<double>(blk);
   c->E32 = ar.take<float>(blk);
-  for (int k = 0; k < 9; ++k) c->mr[k] = ar.take<double>(blk);
+  for (int k = 0; k < 9; ++k) c->mr[k] = ar.take<double>(blk2);
   const int hist = c->o.lbfgs_history;
   c->Sh = ar.take<double>((size_t)hist * L);
   c->Yh = ar.take<double>((size_t)hist * L);
@@ -216,7 +226,8 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   INV_CUDA(h, cudaMemcpyAsync(kA, tabs.data() + N, N * sizeof(double), cudaMemcpyHostToDevice, s));
   INV_CUDA(h, cudaMemcpyAsync(kB, tabs.data() + 2 * N, N * sizeof(double), cudaMemcpyHostToDevice, s));
   ::invdft::count_launch();
-  init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag);
+  init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag,
+                                             h->precf);
   INV_LAUNCH(h, "init_fields");
   std::vector<float> ke;
   std::vector<int> perm;
@@ -232,6 +243,7 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   }
   INV_CUDA(h, cudaMemsetAsync(h->status, 0, 16 * sizeof(int), s));
   INV_CUDA(h, cudaMemsetAsync(h->v, 0, h->L * sizeof(double), s));
+  INV_CUDA(h, cudaMemsetAsync(h->vf, 0, h->L * sizeof(float), s));
   INV_CUDA(h, cudaMemsetAsync(h->vfixed, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaStreamSynchronize(s));   // host tables above are freed on return
   h->g.dm1 = h->dm1;
@@ -282,7 +294,7 @@ invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed, const
   cudaStream_t s = (cudaStream_t)stream;
   INV_CUDA(h, cudaMemcpyAsync(h->vfixed, v_fixed, h->L * sizeof(double), cudaMemcpyDeviceToDevice, s));
   ::invdft::count_launch();
-  add_fields<<<grid_for(h->L), 256, 0, s>>>(v_fixed, v_xc, h->v, h->L);
+  add_fields<<<grid_for(h->L), 256, 0, s>>>(v_fixed, v_xc, h->v, h->vf, h->L);
   INV_LAUNCH(h, "add_fields");
   h->have_potential = true;
   h->have_forward = false;

@@ -337,166 +337,6 @@ cudaError_t launch_fill_random(double *X, long long n, unsigned long long seed, 
 
 }  // namespace invdft
 
-// ---------------------------------------------------------------------------
-// Tall-skinny FP32 kernels for the deflation of the MINRES blocks
-// (Z <- Z - Psi (Psi^T Z), n1, n2 <= 64).
-namespace invdft {
-namespace {
-
-constexpr int kTsRows = 32;       // rows per staged chunk
-constexpr int kTsLd = 68;         // padded row length in shared memory
-
-// partial[b][i][j] = sum over the rows of CTA b of A[a][i] B[a][j]; FP32
-// accumulation of a 4x4 tile per thread, chunks double-buffered in shared
-// memory with cp.async so that the next chunk loads while this one is used.
-__global__ void __launch_bounds__(256) ts_gram_f32(const float *__restrict__ A, int n1,
-                                                   const float *__restrict__ B, int n2,
-                                                   long long L, double *__restrict__ partial) {
-  __shared__ __align__(16) float sA[2][kTsRows][kTsLd];
-  __shared__ __align__(16) float sB[2][kTsRows][kTsLd];
-  const int tid = threadIdx.x;
-  const int ti = tid / 16, tj = tid % 16;
-  const long long rows_per = ((L + gridDim.x - 1) / gridDim.x + kTsRows - 1) / kTsRows * kTsRows;
-  const long long r_begin = blockIdx.x * rows_per;
-  const long long r_end = min(L, r_begin + rows_per);
-  float acc[4][4] = {};
-  auto stage = [&](int buf, long long r0) {
-    // rows r0..r0+31 of A and B (contiguous blocks), 4-byte cp.async
-    const int na = kTsRows * n1, nbb = kTsRows * n2;
-    for (int e = tid; e < na; e += 256) {
-      const int r = e / n1, c = e - r * n1;
-      float *dst = &sA[buf][r][c];
-      if (r0 + r < r_end) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
-                     :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(A + (r0 + r) * n1 + c));
-      } else {
-        *dst = 0.f;
-      }
-    }
-    for (int e = tid; e < nbb; e += 256) {
-      const int r = e / n2, c = e - r * n2;
-      float *dst = &sB[buf][r][c];
-      if (r0 + r < r_end) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
-                     :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(B + (r0 + r) * n2 + c));
-      } else {
-        *dst = 0.f;
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  // zero the padding columns once (never written by the copies)
-  for (int e = tid; e < 2 * kTsRows; e += 256) {
-    const int buf = e / kTsRows, r = e % kTsRows;
-    for (int c = n1; c < kTsLd; ++c) sA[buf][r][c] = 0.f;
-    for (int c = n2; c < kTsLd; ++c) sB[buf][r][c] = 0.f;
-  }
-  __syncthreads();
-  int buf = 0;
-  if (r_begin < r_end) stage(0, r_begin);
-  for (long long r0 = r_begin; r0 < r_end; r0 += kTsRows) {
-    const bool more = r0 + kTsRows < r_end;
-    if (more) stage(buf ^ 1, r0 + kTsRows);
-    if (more) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-#pragma unroll 8
-    for (int r = 0; r < kTsRows; ++r) {
-      const float4 a = *reinterpret_cast<const float4 *>(&sA[buf][r][ti * 4]);
-      const float4 b = *reinterpret_cast<const float4 *>(&sB[buf][r][tj * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int x = 0; x < 4; ++x)
-#pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
-    }
-    __syncthreads();
-    buf ^= 1;
-  }
-  double *out = partial + (size_t)blockIdx.x * n1 * n2;
-#pragma unroll
-  for (int x = 0; x < 4; ++x)
-#pragma unroll
-    for (int y = 0; y < 4; ++y) {
-      const int i = ti * 4 + x, j = tj * 4 + y;
-      if (i < n1 && j < n2) out[i * n2 + j] = (double)acc[x][y];
-    }
-}
-
-__global__ void ts_sum_partials(const double *__restrict__ partial, int nblk, int n,
-                                double *__restrict__ G) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * n + e];
-  G[e] = s;
-}
-
-// Z[a][j] += sum_i Psi[a][i] Cf[i][j] with Cf = alpha * C in FP32; a CTA owns
-// 128 rows; warp w handles rows (w % 4) * 32 + lane and columns
-// [32 * (w / 4), +32) with 32 register accumulators.
-__global__ void __launch_bounds__(256) ts_rotate_f32(const float *__restrict__ Psi, int n1,
-                                                     const double *__restrict__ C, int n2,
-                                                     long long L, float *__restrict__ Z,
-                                                     double alpha) {
-  __shared__ float sC[64][64];
-  __shared__ float sP[128][65];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int i = e / 64, j = e % 64;
-    sC[i][j] = (i < n1 && j < n2) ? (float)(alpha * C[i * n2 + j]) : 0.f;
-  }
-  const int rloc = (warp & 3) * 32 + lane;
-  const int j0 = (warp >> 2) * 32;
-  for (long long a0 = (long long)blockIdx.x * 128; a0 < L; a0 += (long long)gridDim.x * 128) {
-    __syncthreads();
-    const int rows = (int)min((long long)128, L - a0);
-    for (int e = tid; e < 128 * n1; e += 256) {
-      const int r = e / n1, i = e - r * n1;
-      sP[r][i] = r < rows ? Psi[(a0 + r) * n1 + i] : 0.f;
-    }
-    __syncthreads();
-    if (j0 >= n2) continue;
-    float acc[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-    for (int i = 0; i < n1; ++i) {
-      const float psi = sP[rloc][i];
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = fmaf(psi, sC[i][j0 + j], acc[j]);
-    }
-    if (rloc < rows) {
-      float *zr = Z + (a0 + rloc) * n2;
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j0 + j < n2) zr[j0 + j] += acc[j];
-    }
-  }
-}
-
-int ts_grid(long long L) { return (int)std::min<long long>((L + 127) / 128, 148LL * 8); }
-
-}  // namespace
-
-cudaError_t launch_deflate_gram_f32(const float *Psi, int n1, const float *Z, int n2, long long L,
-                                    double *G, double *partial, cudaStream_t s) {
-  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
-  ::invdft::count_launch();
-  ts_gram_f32<<<kGramBlocks, 256, 0, s>>>(Psi, n1, Z, n2, L, partial);
-  ::invdft::count_launch();
-  ts_sum_partials<<<(n1 * n2 + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, n1 * n2, G);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_deflate_update_f32(const float *Psi, int n1, const double *C, int n2,
-                                      long long L, float *Z, double alpha, cudaStream_t s) {
-  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
-  ::invdft::count_launch();
-  ts_rotate_f32<<<ts_grid(L), 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha);
-  return cudaGetLastError();
-}
-
-}  // namespace invdft
 
 // ---------------------------------------------------------------------------
 // Row-striped tall-skinny Gram for any n1, n2 <= 64: a thread owns a 4x4
@@ -698,110 +538,175 @@ template cudaError_t launch_stripe_rotate<double>(const double *, int, const dou
 }  // namespace invdft
 
 // ---------------------------------------------------------------------------
-// Register-tiled FP32 deflation update with an optional fused column dot:
-//   Z[a][j] += sum_i Psi[a][i] (alpha C)[i][j]         (n1, n2 <= 64)
-//   partial[b][j] = sum over the rows of CTA b of V[a][j] Z_new[a][j]
-// A thread owns 8 rows x 4 columns of a 128 x 64 tile; Psi rows are staged in
-// shared memory, C is resident.
+// Both Gram matrices of the Rayleigh-Ritz step (Eq. 23), S = Y^T Y and
+// Hs = Y^T (H~Y), in FP64 from one pass over Y and H~Y.  Both are symmetric,
+// so only the 4 x 4 tiles on or above the diagonal are formed (about half the
+// FP64 FMAs of two full Grams); the final sum mirrors them.
 namespace invdft {
 namespace {
 
-template <bool DOT>
-__global__ void __launch_bounds__(256) defl_update_f32(const float *__restrict__ Psi, int n1,
-                                                       const double *__restrict__ C, int n2,
-                                                       long long L, float *__restrict__ Z,
-                                                       double alpha, const float *__restrict__ V,
-                                                       double *__restrict__ partial) {
-  __shared__ __align__(16) float sC[64][64];
-  __shared__ float sP[128 * 65];
-  __shared__ double red[16][64];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int ld = n1 + 1;
-  for (int e = tid; e < 64 * 64; e += 256) {
-    const int i = e / 64, j = e % 64;
-    sC[i][j] = (i < n1 && j < n2) ? (float)(alpha * C[i * n2 + j]) : 0.f;
+constexpr int kRrRows = 32;
+constexpr int kRrTasks = 3;          // tiles per thread (n <= 96: 2 x 300 tiles)
+
+__device__ __forceinline__ void tri_tile(int k, int T, int &ti, int &tj) {
+  ti = 0;
+  while (k >= T - ti) {
+    k -= T - ti;
+    ++ti;
   }
-  double dsum[4] = {0.0, 0.0, 0.0, 0.0};
-  for (long long a0 = (long long)blockIdx.x * 128; a0 < L; a0 += (long long)gridDim.x * 128) {
-    __syncthreads();
-    const int rows = (int)min((long long)128, L - a0);
-    const float *src = Psi + a0 * n1;
-    for (int e = tid; e < rows * n1; e += 256) {
-      const int r = e / n1, i = e - r * n1;
-      sP[r * ld + i] = __ldg(src + e);
-    }
-    __syncthreads();
-    float acc[8][4];
+  tj = ti + k;
+}
+
+__global__ void __launch_bounds__(256) gram_rr_kernel(const double *__restrict__ Y,
+                                                      const double *__restrict__ HY, int n,
+                                                      long long L, double *__restrict__ partial) {
+  extern __shared__ __align__(16) double rsm[];
+  double *sY = rsm;                          // [2][kRrRows][n]
+  double *sH = rsm + 2 * kRrRows * n;        // [2][kRrRows][n]
+  const int tid = threadIdx.x;
+  const int T = (n + 3) / 4, NT = T * (T + 1) / 2, ntask = 2 * NT;
+  // ntask <= 256: one tile per thread, spare threads split the rows into
+  // S stripes; otherwise up to kRrTasks tiles per thread
+  const int S = ntask <= 256 ? min(kRrRows, 256 / ntask) : 1;
+  const int stripe = ntask <= 256 ? tid / ntask : 0;
+  const int tbase = ntask <= 256 ? tid - stripe * ntask : tid;
+  int i0[kRrTasks], j0[kRrTasks];
+  bool hs[kRrTasks], on[kRrTasks];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+  for (int m = 0; m < kRrTasks; ++m) {
+    const int t = tbase + 256 * m;
+    on[m] = t < ntask && stripe < S;
+    int ti = 0, tj = 0;
+    if (on[m]) tri_tile(t % NT, T, ti, tj);
+    i0[m] = 4 * ti;
+    j0[m] = 4 * tj;
+    hs[m] = t >= NT;
+  }
+  const long long per = ((L + gridDim.x - 1) / gridDim.x + kRrRows - 1) / kRrRows * kRrRows;
+  const long long r_begin = (long long)blockIdx.x * per;
+  const long long r_end = min(L, r_begin + per);
+  double acc[kRrTasks][4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-    for (int i = 0; i < n1; ++i) {
-      const float4 c4 = *reinterpret_cast<const float4 *>(&sC[i][tx * 4]);
+  for (int m = 0; m < kRrTasks; ++m)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float pv = sP[(ty * 8 + r) * ld + i];
-        acc[r][0] = fmaf(pv, c4.x, acc[r][0]);
-        acc[r][1] = fmaf(pv, c4.y, acc[r][1]);
-        acc[r][2] = fmaf(pv, c4.z, acc[r][2]);
-        acc[r][3] = fmaf(pv, c4.w, acc[r][3]);
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) acc[m][x][y] = 0.0;
+  auto stage = [&](int buf, long long r0) {
+    const int rows = (int)min((long long)kRrRows, r_end - r0);
+    double *dy = sY + buf * kRrRows * n, *dh = sH + buf * kRrRows * n;
+    for (int e = tid; e < kRrRows * n; e += 256) {
+      if (e < rows * n) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(dy + e)), "l"(Y + r0 * n + e)
+                     : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                     :: "r"((unsigned)__cvta_generic_to_shared(dh + e)), "l"(HY + r0 * n + e)
+                     : "memory");
+      } else {
+        dy[e] = 0.0;
+        dh[e] = 0.0;
       }
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  int buf = 0;
+  if (r_begin < r_end) stage(0, r_begin);
+  for (long long r0 = r_begin; r0 < r_end; r0 += kRrRows) {
+    const bool more = r0 + kRrRows < r_end;
+    if (more) {
+      stage(buf ^ 1, r0 + kRrRows);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const double *ry = sY + buf * kRrRows * n, *rh = sH + buf * kRrRows * n;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      const int rr = ty * 8 + r;
-      if (rr >= rows) continue;
-      float *zr = Z + (a0 + rr) * n2;
+    for (int m = 0; m < kRrTasks; ++m) {
+      if (!on[m]) continue;
+      const double *rb = hs[m] ? rh : ry;
+      for (int r = stripe; r < kRrRows; r += S) {
+        double av[4], bv[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int col = tx * 4 + q;
-        if (col < n2) {
-          const float z = zr[col] + acc[r][q];
-          zr[col] = z;
-          if (DOT) dsum[q] += (double)V[(a0 + rr) * n2 + col] * (double)z;
+        for (int x = 0; x < 4; ++x) {
+          av[x] = i0[m] + x < n ? ry[r * n + i0[m] + x] : 0.0;
+          bv[x] = j0[m] + x < n ? rb[r * n + j0[m] + x] : 0.0;
         }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[m][x][y] = fma(av[x], bv[y], acc[m][x][y]);
       }
     }
-  }
-  if (DOT) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) red[ty][tx * 4 + q] = dsum[q];
     __syncthreads();
-    if (tid < n2) {
-      double s = 0.0;
-      for (int k = 0; k < 16; ++k) s += red[k][tid];
-      partial[(size_t)blockIdx.x * kMaxCols + tid] = s;
-    }
+    buf ^= 1;
+  }
+  if (S > 1) {
+    // stripes -> shared memory -> stripe 0 (the staging buffers are idle now)
+    if (on[0])
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) rsm[(size_t)(stripe * ntask + tbase) * 16 + x * 4 + y] = acc[0][x][y];
+    __syncthreads();
+    if (stripe == 0 && on[0])
+      for (int q = 1; q < S; ++q)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[0][x][y] += rsm[(size_t)(q * ntask + tbase) * 16 + x * 4 + y];
+  }
+  if (stripe != 0) return;
+  double *out = partial + (size_t)blockIdx.x * ntask * 16;
+#pragma unroll
+  for (int m = 0; m < kRrTasks; ++m) {
+    if (!on[m]) continue;
+    const int t = tbase + 256 * m;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) out[(size_t)t * 16 + x * 4 + y] = acc[m][x][y];
   }
 }
 
-__global__ void warp_sum_cols(const double *__restrict__ partial, int nblk, int n,
-                              double *__restrict__ out) {
-  const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (e >= n) return;
+// S[i][j], Hs[i][j] from the tile partials of all CTAs (mirrored below the
+// diagonal); e < 2 n^2 indexes S then Hs
+__global__ void gram_rr_sum(const double *__restrict__ partial, int nblk, int n,
+                            double *__restrict__ S, double *__restrict__ Hs) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * n * n) return;
+  const int mat = e / (n * n), r = e - mat * n * n;
+  int i = r / n, j = r - (r / n) * n;
+  if (i / 4 > j / 4) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  const int T = (n + 3) / 4, NT = T * (T + 1) / 2, ti = i / 4, tj = j / 4;
+  const int k = ti * T - ti * (ti - 1) / 2 + (tj - ti);
+  const size_t task = (size_t)mat * NT + k, stride = (size_t)2 * NT * 16;
+  const size_t off = task * 16 + (i % 4) * 4 + (j % 4);
   double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += partial[(size_t)b * kMaxCols + e];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) out[e] = s;
+  for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * stride + off];
+  (mat == 0 ? S : Hs)[r] = s;
 }
 
 }  // namespace
 
-cudaError_t launch_defl_update_f32(const float *Psi, int n1, const double *C, int n2, long long L,
-                                   float *Z, double alpha, const float *V, double *dot_out,
-                                   double *partial, cudaStream_t s) {
-  if (n1 < 1 || n2 < 1 || n1 > 64 || n2 > 64) return cudaErrorInvalidValue;
-  const int grid = (int)std::min<long long>((L + 127) / 128, 148LL * 4);
+cudaError_t launch_gram_rr(const double *Y, const double *HY, int n, long long L, double *S,
+                           double *Hs, double *partial, cudaStream_t s) {
+  const int T = (n + 3) / 4;
+  if (n < 1 || 2 * T * (T + 1) / 2 > 256 * kRrTasks) return cudaErrorInvalidValue;
+  // staging ring, and room for the stripe sums (at most 256 x 16 doubles)
+  const size_t smem = std::max(4 * (size_t)kRrRows * n, (size_t)256 * 16) * sizeof(double);
+  cudaError_t e =
+      cudaFuncSetAttribute(gram_rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   ::invdft::count_launch();
-  if (V) {
-    defl_update_f32<true><<<grid, 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha, V, partial);
-    ::invdft::count_launch();
-    warp_sum_cols<<<(n2 + 7) / 8, 256, 0, s>>>(partial, grid, n2, dot_out);
-  } else {
-    defl_update_f32<false><<<grid, 256, 0, s>>>(Psi, n1, C, n2, L, Z, alpha, nullptr, nullptr);
-  }
+  gram_rr_kernel<<<kGramBlocks, 256, smem, s>>>(Y, HY, n, L, partial);
+  ::invdft::count_launch();
+  gram_rr_sum<<<(2 * n * n + 255) / 256, 256, 0, s>>>(partial, kGramBlocks, n, S, Hs);
   return cudaGetLastError();
 }
 

@@ -36,15 +36,93 @@ __global__ void hx_nodal(const T *__restrict__ X, T *__restrict__ Z, const doubl
 template <typename T>
 __device__ __forceinline__ void atomic_add(T *p, T x) { atomicAdd(p, x); }
 
+// The 1D matrices A and B are centrosymmetric (M[i][j] = M[P-i][P-j] for GLL
+// nodes symmetric about the cell centre), so y = M u splits into an even part
+// on e_k = u_k + u_(P-k) and an odd part on o_k = u_k - u_(P-k):
+//   y_i = ye_i + yo_i,  y_(P-i) = ye_i - yo_i (i < P/2),  y_(P/2) = ye_(P/2),
+// with (P/2+1)^2 + (P/2)^2 coefficients instead of (P+1)^2 (13 instead of 25
+// FMAs for Q4).
+template <int P>
+struct EoTab {
+  static constexpr int H = P / 2, NE = (H + 1) * (H + 1), NO = H * H;
+  double eA[NE], oA[NO], eB[NE], oB[NO];
+};
+
+template <int P>
+EoTab<P> make_eo(const Geom &g) {
+  constexpr int Q = P + 1, H = P / 2;
+  EoTab<P> t;
+  auto sym = [&](const double *M, int i, int j) {
+    return 0.5 * (M[i * Q + j] + M[(P - i) * Q + (P - j)]);
+  };
+  for (int m = 0; m < 2; ++m) {
+    const double *M = m == 0 ? g.A : g.B;
+    double *e = m == 0 ? t.eA : t.eB, *o = m == 0 ? t.oA : t.oB;
+    for (int i = 0; i <= H; ++i)
+      for (int k = 0; k <= H; ++k)
+        e[i * (H + 1) + k] = k < H ? 0.5 * (sym(M, i, k) + sym(M, i, P - k)) : sym(M, i, H);
+    for (int i = 0; i < H; ++i)
+      for (int k = 0; k < H; ++k) o[i * H + k] = 0.5 * (sym(M, i, k) - sym(M, i, P - k));
+  }
+  return t;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void eo_split(const T *u, T *e, T *o) {
+  constexpr int H = P / 2;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    e[k] = u[k] + u[P - k];
+    o[k] = u[k] - u[P - k];
+  }
+  e[H] = u[H];
+}
+
+// y = M1 u1 (+ M2 u2) from the even/odd parts of u1 (and u2)
+template <typename T, int P, bool TWO>
+__device__ __forceinline__ void eo_apply(const T *e1, const T *o1, const T *eM1, const T *oM1,
+                                         const T *e2, const T *o2, const T *eM2, const T *oM2,
+                                         T *y) {
+  constexpr int H = P / 2;
+  T ye[H + 1], yo[H > 0 ? H : 1];
+#pragma unroll
+  for (int i = 0; i <= H; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k <= H; ++k) {
+      s += eM1[i * (H + 1) + k] * e1[k];
+      if (TWO) s += eM2[i * (H + 1) + k] * e2[k];
+    }
+    ye[i] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      s += oM1[i * H + k] * o1[k];
+      if (TWO) s += oM2[i * H + k] * o2[k];
+    }
+    yo[i] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    y[i] = ye[i] + yo[i];
+    y[P - i] = ye[i] - yo[i];
+  }
+  y[H] = ye[H];
+}
+
 // One CTA per (cell, chunk of C columns).  Two shared buffers of (p+1)^3 x C.
 template <typename T, int P, int C>
 __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__restrict__ Z,
-                                                int ncol, Geom g, double scale) {
-  constexpr int Q = P + 1, NE = Q * Q * Q;
+                                                int ncol, Geom g, EoTab<P> tab, double scale) {
+  constexpr int Q = P + 1, NE = Q * Q * Q, H = P / 2;
+  constexpr int NEC = EoTab<P>::NE, NOC = EoTab<P>::NO;
   extern __shared__ unsigned char smem_raw[];
   T *u = reinterpret_cast<T *>(smem_raw);
   T *w = u + NE * C;
-  __shared__ T sA[Q * Q], sB[Q * Q];
+  __shared__ T eA[NEC], oA[NOC > 0 ? NOC : 1], eB[NEC], oB[NOC > 0 ? NOC : 1];
   __shared__ double dl[3][Q];
   __shared__ int gidx[3][Q];
 
@@ -54,9 +132,13 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
   const int c0 = blockIdx.y * C;
   const int tid = threadIdx.x;
 
-  if (tid < Q * Q) {
-    sA[tid] = (T)g.A[tid];
-    sB[tid] = (T)g.B[tid];
+  if (tid < NEC) {
+    eA[tid] = (T)tab.eA[tid];
+    eB[tid] = (T)tab.eB[tid];
+  }
+  if (tid < NOC) {
+    oA[tid] = (T)tab.oA[tid];
+    oB[tid] = (T)tab.oB[tid];
   }
   if (tid < 3 * Q) {
     const int d = tid / Q, l = tid % Q;
@@ -85,19 +167,16 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
   for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
     const int j = idx % C, line = idx / C;
     const int base = line * Q;
-    T in[Q];
+    T in[Q], e[H + 1], o[H > 0 ? H : 1], yb[Q], ya[Q];
 #pragma unroll
     for (int x = 0; x < Q; ++x) in[x] = u[(base + x) * C + j];
+    eo_split<T, P>(in, e, o);
+    eo_apply<T, P, false>(e, o, eB, oB, e, o, eB, oB, yb);
+    eo_apply<T, P, false>(e, o, eA, oA, e, o, eA, oA, ya);
 #pragma unroll
     for (int xo = 0; xo < Q; ++xo) {
-      T sb = 0, sa = 0;
-#pragma unroll
-      for (int x = 0; x < Q; ++x) {
-        sb += sB[xo * Q + x] * in[x];
-        sa += sA[xo * Q + x] * in[x];
-      }
-      u[(base + xo) * C + j] = sb;
-      w[(base + xo) * C + j] = sa;
+      u[(base + xo) * C + j] = yb[xo];
+      w[(base + xo) * C + j] = ya[xo];
     }
   }
   __syncthreads();
@@ -106,22 +185,20 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
   for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
     const int j = idx % C, r = idx / C;
     const int x = r % Q, z = r / Q;
-    T t1[Q], t2[Q];
+    T t1[Q], t2[Q], e1[H + 1], o1[H > 0 ? H : 1], e2[H + 1], o2[H > 0 ? H : 1], y1[Q], y2[Q];
 #pragma unroll
     for (int y = 0; y < Q; ++y) {
       t1[y] = u[(x + Q * (y + Q * z)) * C + j];
       t2[y] = w[(x + Q * (y + Q * z)) * C + j];
     }
+    eo_split<T, P>(t1, e1, o1);
+    eo_split<T, P>(t2, e2, o2);
+    eo_apply<T, P, false>(e1, o1, eB, oB, e1, o1, eB, oB, y1);
+    eo_apply<T, P, true>(e1, o1, eA, oA, e2, o2, eB, oB, y2);
 #pragma unroll
     for (int yo = 0; yo < Q; ++yo) {
-      T s11 = 0, q = 0;
-#pragma unroll
-      for (int y = 0; y < Q; ++y) {
-        s11 += sB[yo * Q + y] * t1[y];
-        q += sA[yo * Q + y] * t1[y] + sB[yo * Q + y] * t2[y];
-      }
-      u[(x + Q * (yo + Q * z)) * C + j] = s11;
-      w[(x + Q * (yo + Q * z)) * C + j] = q;
+      u[(x + Q * (yo + Q * z)) * C + j] = y1[yo];
+      w[(x + Q * (yo + Q * z)) * C + j] = y2[yo];
     }
   }
   __syncthreads();
@@ -130,19 +207,17 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
   for (int idx = tid; idx < Q * Q * C; idx += blockDim.x) {
     const int j = idx % C, r = idx / C;
     const int x = r % Q, y = r / Q;
-    T t1[Q], t2[Q];
+    T t1[Q], t2[Q], e1[H + 1], o1[H > 0 ? H : 1], e2[H + 1], o2[H > 0 ? H : 1], yz[Q];
 #pragma unroll
     for (int z = 0; z < Q; ++z) {
       t1[z] = u[(x + Q * (y + Q * z)) * C + j];
       t2[z] = w[(x + Q * (y + Q * z)) * C + j];
     }
+    eo_split<T, P>(t1, e1, o1);
+    eo_split<T, P>(t2, e2, o2);
+    eo_apply<T, P, true>(e1, o1, eA, oA, e2, o2, eB, oB, yz);
 #pragma unroll
-    for (int zo = 0; zo < Q; ++zo) {
-      T s = 0;
-#pragma unroll
-      for (int z = 0; z < Q; ++z) s += sA[zo * Q + z] * t1[z] + sB[zo * Q + z] * t2[z];
-      u[(x + Q * (y + Q * zo)) * C + j] = s;
-    }
+    for (int zo = 0; zo < Q; ++zo) u[(x + Q * (y + Q * zo)) * C + j] = yz[zo];
   }
   __syncthreads();
 
@@ -168,7 +243,7 @@ cudaError_t run_cells(const Geom &g, const T *X, T *Z, int ncol, double scale, c
   if (e != cudaSuccess) return e;
   dim3 grid(g.ncell * g.ncell * g.ncell, (ncol + C - 1) / C);
   ::invdft::count_launch();
-  k<<<grid, 256, smem, s>>>(X, Z, ncol, g, scale);
+  k<<<grid, 256, smem, s>>>(X, Z, ncol, g, make_eo<P>(g), scale);
   return cudaGetLastError();
 }
 
@@ -219,8 +294,9 @@ cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
   const bool tc = a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
                   (const void *)a.Z != (const void *)a.E;
   if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + 8, s);
-  const bool simt_q4 = c->g.p == 4 && c->cell_perm && !a.E && a.Z != a.X && a.Z != a.W;
-  if (simt_q4) return launch_hx_simt_q4(c->g, c->v, a, c->cell_perm, s);
+  const bool simt_q4 = c->g.p == 4 && c->cell_perm && a.Z != a.X && a.Z != a.W &&
+                       (const void *)a.Z != (const void *)a.E;
+  if (simt_q4) return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, s);
   return launch_hx(c->g, c->v, a, s);
 }
 

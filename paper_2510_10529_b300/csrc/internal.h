@@ -94,9 +94,11 @@ struct Ctx {
   double *mass = nullptr;           // [L]
   double *dvec = nullptr;           // [L]  m^-1/2
   double *prec_diag = nullptr;      // [L]  1 / diag(D K D)
+  float *precf = nullptr;           // [L]  FP32 copy (FP32 MINRES)
   float *Ke_tc = nullptr;           // 128 x 128 TF32 cell matrix in the UMMA layout (Q4)
   int *cell_perm = nullptr;         // [ncell^3] visiting order of the tensor-core kernel
   double *v = nullptr;              // [L]  total potential
+  float *vf = nullptr;              // [L]  FP32 copy (FP32 CUDA-core H~X)
   double *vfixed = nullptr;         // [L]
   double *X = nullptr;              // [L][nv] orbitals (FP64)
   double *Y = nullptr;              // [L][nv]
@@ -192,7 +194,7 @@ size_t tc_cell_matrix_floats();
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
                          const int *perm, int *err, cudaStream_t s);
 void build_cell_order(int nc, std::vector<int> *perm);
-cudaError_t launch_hx_simt_q4(const Geom &g, const double *v, const HxArgs<float> &a,
+cudaError_t launch_hx_simt_q4(const Geom &g, const float *vf, const HxArgs<float> &a,
                               const int *perm, cudaStream_t s);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
@@ -204,12 +206,6 @@ cudaError_t launch_gram_f32(const float *A, int n1, const float *B, int n2, long
 // FP32 inputs, FP32 accumulation inside a CTA, FP64 across CTAs
 cudaError_t launch_gram_f32acc(const float *A, int n1, const float *B, int n2, long long L,
                                double *G, double *partial, cudaStream_t s);
-// FP32 tall-skinny pair for the deflation of MINRES blocks (n1, n2 <= 64):
-// G = Psi^T Z (FP32 within a CTA, FP64 across CTAs) and Z += alpha Psi C
-cudaError_t launch_deflate_gram_f32(const float *Psi, int n1, const float *Z, int n2, long long L,
-                                    double *G, double *partial, cudaStream_t s);
-cudaError_t launch_deflate_update_f32(const float *Psi, int n1, const double *C, int n2,
-                                      long long L, float *Z, double alpha, cudaStream_t s);
 // Row-striped tall-skinny Gram (n1, n2 <= 64) and row-tiled update
 // (n1, n2 <= 128): G = A^T B, Z += alpha Psi C
 template <typename T, typename TA>
@@ -218,11 +214,27 @@ cudaError_t launch_stripe_gram(const T *A, int n1, const T *B, int n2, long long
 template <typename T>
 cudaError_t launch_stripe_rotate(const T *Psi, int n1, const double *C, int n2, long long L, T *Z,
                                  double alpha, cudaStream_t s);
-// Register-tiled FP32 update Z += alpha Psi C (n1, n2 <= 64); with V != null
-// also dot_out[j] = sum_a V[a][j] Z_new[a][j] (FP64 accumulation)
-cudaError_t launch_defl_update_f32(const float *Psi, int n1, const double *C, int n2, long long L,
-                                   float *Z, double alpha, const float *V, double *dot_out,
-                                   double *partial, cudaStream_t s);
+// S = Y^T Y and Hs = Y^T HY (both n x n, symmetric by construction: the upper
+// 4 x 4 tiles are formed and mirrored), n <= 96
+cudaError_t launch_gram_rr(const double *Y, const double *HY, int n, long long L, double *S,
+                           double *Hs, double *partial, cudaStream_t s);
+// FP32 deflation pair for MINRES blocks (deflate.cu).  Widths n1p (a multiple
+// of 8) and n2p (a multiple of 4) are at most 64 (zero padding columns),
+// blocks 16-byte aligned.
+// G[i*n2p + j] = sum_a Psi[a][i] Z[a][j] (FP32 within a CTA, FP64 across CTAs)
+cudaError_t launch_defl_gram_f32(const float *Psi, int n1p, const float *Z, int n2p, long long L,
+                                 double *G, double *partial, cudaStream_t s);
+// Z += alpha Psi C (C is n1p x n2p, FP64); with V != null also
+// dot_out[j] = sum_a V[a][j] Z_new[a][j] (FP32 within a tile, FP64 across)
+cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, int n2p,
+                                   long long L, float *Z, double alpha, const float *V,
+                                   double *dot_out, double *partial, cudaStream_t s);
+// F[a][j] = j < n ? X[a][j] : 0 for j < np (FP64 -> FP32 with zero padding)
+cudaError_t launch_convert_pad_f32(const double *X, int n, int np, long long L, float *F,
+                                   cudaStream_t s);
+// P[a][j] += F[a][j] for j < n (FP32 padded block of width np into FP64)
+cudaError_t launch_add_unpad(const float *F, int np, double *P, int n, long long L,
+                             cudaStream_t s);
 // Xo += alpha * Xi Cm  (n1 -> n2 columns) in the storage precision T
 template <typename T>
 cudaError_t launch_rotate_acc(const T *Xi, int n1, const double *Cm, int n2, long long L, T *Xo,

@@ -217,108 +217,156 @@ __global__ void scale_f32_kernel(const float *__restrict__ E, double alpha, int 
   GRID_STRIDE(e, L * n) D[e] = (float)(alpha * (double)E[e]);
 }
 
+// st layout: st[k * n + c] for scalar k (kMr* in solvers.h) of column c
+__global__ void mr_givens_kernel(int n, double *__restrict__ st) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  auto S = [&](int k) -> double & { return st[(size_t)k * n + c]; };
+  const double bn = sqrt(fmax(S(kMrBnext), 0.0));
+  auto retire = [&]() {
+    S(kMrEps) = S(kMrDel) = S(kMrIg) = S(kMrT) = 0.0;
+    S(kMrIbp) = S(kMrIb);
+    S(kMrIb) = 0.0;
+  };
+  if (S(kMrActive) == 0.0) {
+    retire();
+    return;
+  }
+  const double a = S(kMrAlpha), b = S(kMrBeta);
+  const double eps_k = S(kMrSpp) * b;
+  const double tmp = S(kMrCpp) * b;
+  const double delta = S(kMrCp) * tmp + S(kMrSp) * a;
+  const double gbar = -S(kMrSp) * tmp + S(kMrCp) * a;
+  const double gamma = hypot(gbar, bn);
+  if (!(gamma > 0.0)) {
+    S(kMrActive) = 0.0;
+    retire();
+    return;
+  }
+  const double cs = gbar / gamma, sn = bn / gamma;
+  const double t = cs * S(kMrPhibar);
+  S(kMrPhibar) = -sn * S(kMrPhibar);
+  S(kMrEps) = eps_k;
+  S(kMrDel) = delta;
+  S(kMrIg) = 1.0 / gamma;
+  S(kMrT) = t;
+  S(kMrCpp) = S(kMrCp);
+  S(kMrSpp) = S(kMrSp);
+  S(kMrCp) = cs;
+  S(kMrSp) = sn;
+  S(kMrBeta) = bn;
+  S(kMrIbp) = S(kMrIb);
+  S(kMrIb) = bn > 0.0 ? 1.0 / bn : 0.0;
+  S(kMrRel) = fabs(S(kMrPhibar)) / S(kMrBeta1);
+  S(kMrIters) += 1.0;
+  if (S(kMrRel) <= S(kMrTol) || bn == 0.0) S(kMrActive) = 0.0;
+}
+
 template <typename T>
-__global__ void mr_lanczos_kernel(const T *__restrict__ p, const T *__restrict__ q,
-                                  const T *__restrict__ qprev, const double *__restrict__ alpha,
-                                  const double *__restrict__ beta, const double *__restrict__ prec,
-                                  int n, long long L, T *__restrict__ qhat, T *__restrict__ zhat,
-                                  FastDiv fd) {
-  __shared__ T sa[kMaxCols], sb[kMaxCols];
+__global__ void mr_step_kernel(const T *__restrict__ ph, const T *__restrict__ qh,
+                               T *__restrict__ qo, T *__restrict__ zo, T *__restrict__ wpp,
+                               const T *__restrict__ wp, T *__restrict__ x,
+                               double *__restrict__ st, const double *__restrict__ prec, int n,
+                               long long L, FastDiv fd) {
+  __shared__ T c1[kMaxCols], c2[kMaxCols], c3[kMaxCols], cz[kMaxCols];
+  __shared__ T ce[kMaxCols], cd[kMaxCols], cg[kMaxCols], ct[kMaxCols];
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    sa[c] = (T)alpha[c];
-    sb[c] = (T)beta[c];
+    const double sk = st[kMrIb * n + c], skm = st[kMrIbp * n + c], bk = st[kMrBeta * n + c];
+    const bool on = st[kMrActive * n + c] != 0.0;
+    const double alpha = sk * sk * st[kMrRaw * n + c];
+    if (blockIdx.x == 0) st[kMrAlpha * n + c] = alpha;
+    c1[c] = on ? (T)sk : (T)0;
+    c2[c] = on ? (T)(-alpha * sk) : (T)0;
+    c3[c] = on ? (T)(-bk * skm) : (T)0;
+    cz[c] = (T)skm;
+    ce[c] = (T)st[kMrEps * n + c];
+    cd[c] = (T)st[kMrDel * n + c];
+    cg[c] = (T)st[kMrIg * n + c];
+    ct[c] = (T)st[kMrT * n + c];
   }
   __syncthreads();
   GRID_STRIDE32(e, L * n) {
     const uint32_t a = fdiv(e, fd);
     const int c = (int)(e - a * (uint32_t)n);
-    const T r = p[e] - sa[c] * q[e] - sb[c] * qprev[e];
-    qhat[e] = r;
-    zhat[e] = (T)prec[a] * r;
-  }
-}
-
-// st layout: st[k * n + c] for scalar k of column c (see kMr* in solvers.cu)
-__global__ void mr_givens_kernel(int n, double *__restrict__ st) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  double *alpha = st, *beta = st + n, *bnext = st + 2 * n, *cpp = st + 3 * n, *spp = st + 4 * n;
-  double *cp = st + 5 * n, *sp = st + 6 * n, *phibar = st + 7 * n, *beta1 = st + 8 * n;
-  double *active = st + 9 * n, *ceps = st + 10 * n, *cdel = st + 11 * n, *cig = st + 12 * n;
-  double *ct = st + 13 * n, *cib = st + 14 * n, *relres = st + 15 * n, *tol = st + 16 * n;
-  double *iters = st + 17 * n;
-  const double bn = sqrt(fmax(bnext[c], 0.0));
-  if (active[c] == 0.0) {
-    ceps[c] = cdel[c] = cig[c] = ct[c] = 0.0;
-    cib[c] = 0.0;
-    return;
-  }
-  const double a = alpha[c], b = beta[c];
-  const double eps_k = spp[c] * b;
-  const double tmp = cpp[c] * b;
-  const double delta = cp[c] * tmp + sp[c] * a;
-  const double gbar = -sp[c] * tmp + cp[c] * a;
-  const double gamma = hypot(gbar, bn);
-  if (!(gamma > 0.0)) {
-    active[c] = 0.0;
-    ceps[c] = cdel[c] = cig[c] = ct[c] = cib[c] = 0.0;
-    return;
-  }
-  const double cs = gbar / gamma, sn = bn / gamma;
-  const double t = cs * phibar[c];
-  phibar[c] = -sn * phibar[c];
-  ceps[c] = eps_k;
-  cdel[c] = delta;
-  cig[c] = 1.0 / gamma;
-  ct[c] = t;
-  cpp[c] = cp[c];
-  spp[c] = sp[c];
-  cp[c] = cs;
-  sp[c] = sn;
-  beta[c] = bn;
-  cib[c] = bn > 0.0 ? 1.0 / bn : 0.0;
-  relres[c] = fabs(phibar[c]) / beta1[c];
-  iters[c] += 1.0;
-  if (relres[c] <= tol[c] || bn == 0.0) active[c] = 0.0;
-}
-
-template <typename T>
-__global__ void mr_update_kernel(T *__restrict__ z, const T *__restrict__ zhat,
-                                 T *__restrict__ qn, const T *__restrict__ qhat,
-                                 T *__restrict__ wpp, const T *__restrict__ wp,
-                                 T *__restrict__ x, const double *__restrict__ st, int n,
-                                 long long L, FastDiv fd) {
-  __shared__ T se[kMaxCols], sd[kMaxCols], sg[kMaxCols], st_[kMaxCols], sib[kMaxCols];
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    se[c] = (T)st[10 * n + c];
-    sd[c] = (T)st[11 * n + c];
-    sg[c] = (T)st[12 * n + c];
-    st_[c] = (T)st[13 * n + c];
-    sib[c] = (T)st[14 * n + c];
-  }
-  __syncthreads();
-  GRID_STRIDE32(e, L * n) {
-    const int c = (int)(e - fdiv(e, fd) * (uint32_t)n);
-    const T w = (z[e] - se[c] * wpp[e] - sd[c] * wp[e]) * sg[c];
+    const T w = (cz[c] * zo[e] - ce[c] * wpp[e] - cd[c] * wp[e]) * cg[c];
     wpp[e] = w;
-    x[e] = x[e] + st_[c] * w;
-    qn[e] = qhat[e] * sib[c];
-    z[e] = zhat[e] * sib[c];
+    x[e] += ct[c] * w;
+    const T q = c1[c] * ph[e] + c2[c] * qh[e] + c3[c] * qo[e];
+    qo[e] = q;
+    zo[e] = (T)prec[a] * q;
+  }
+}
+
+// mr_step_kernel for FP32 blocks whose width is a multiple of 4: one thread
+// per (node, column quad), float4 loads and stores
+__global__ void mr_step_vec4_kernel(const float4 *__restrict__ ph, const float4 *__restrict__ qh,
+                                    float4 *__restrict__ qo, float4 *__restrict__ zo,
+                                    float4 *__restrict__ wpp, const float4 *__restrict__ wp,
+                                    float4 *__restrict__ x, double *__restrict__ st,
+                                    const double *__restrict__ prec, int n, long long L,
+                                    FastDiv fd4) {
+  __shared__ float4 c1[kMaxCols / 4], c2[kMaxCols / 4], c3[kMaxCols / 4], cz[kMaxCols / 4];
+  __shared__ float4 ce[kMaxCols / 4], cd[kMaxCols / 4], cg[kMaxCols / 4], ct[kMaxCols / 4];
+  float *f1 = reinterpret_cast<float *>(c1), *f2 = reinterpret_cast<float *>(c2);
+  float *f3 = reinterpret_cast<float *>(c3), *fz = reinterpret_cast<float *>(cz);
+  float *fe = reinterpret_cast<float *>(ce), *fdl = reinterpret_cast<float *>(cd);
+  float *fg = reinterpret_cast<float *>(cg), *ft = reinterpret_cast<float *>(ct);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const double sk = st[kMrIb * n + c], skm = st[kMrIbp * n + c], bk = st[kMrBeta * n + c];
+    const bool on = st[kMrActive * n + c] != 0.0;
+    const double alpha = sk * sk * st[kMrRaw * n + c];
+    if (blockIdx.x == 0) st[kMrAlpha * n + c] = alpha;
+    f1[c] = on ? (float)sk : 0.f;
+    f2[c] = on ? (float)(-alpha * sk) : 0.f;
+    f3[c] = on ? (float)(-bk * skm) : 0.f;
+    fz[c] = (float)skm;
+    fe[c] = (float)st[kMrEps * n + c];
+    fdl[c] = (float)st[kMrDel * n + c];
+    fg[c] = (float)st[kMrIg * n + c];
+    ft[c] = (float)st[kMrT * n + c];
+  }
+  __syncthreads();
+  const int n4 = n / 4;
+  GRID_STRIDE32(e, L * n4) {
+    const uint32_t a = fdiv(e, fd4);
+    const int c = (int)(e - a * (uint32_t)n4);
+    const float4 z0 = zo[e], w2 = wpp[e], w1 = wp[e], x0 = x[e];
+    const float4 p0 = ph[e], q1 = qh[e], q0 = qo[e];
+    const float4 a1 = c1[c], a2 = c2[c], a3 = c3[c], az = cz[c];
+    const float4 ae = ce[c], ad = cd[c], ag = cg[c], at = ct[c];
+    const float pr = (float)prec[a];
+    float4 w, xn, q, z;
+#define MR_LANE(k)                                                      \
+  w.k = (az.k * z0.k - ae.k * w2.k - ad.k * w1.k) * ag.k;               \
+  xn.k = fmaf(at.k, w.k, x0.k);                                         \
+  q.k = a1.k * p0.k + a2.k * q1.k + a3.k * q0.k;                        \
+  z.k = pr * q.k;
+    MR_LANE(x) MR_LANE(y) MR_LANE(z) MR_LANE(w)
+#undef MR_LANE
+    wpp[e] = w;
+    x[e] = xn;
+    qo[e] = q;
+    zo[e] = z;
   }
 }
 
 template <typename T>
-__global__ void mr_init_kernel(const T *__restrict__ b, const T *__restrict__ zb,
-                               const double *__restrict__ beta1, int n, long long L,
-                               T *__restrict__ q, T *__restrict__ z, FastDiv fd) {
-  __shared__ T sib[kMaxCols];
-  for (int c = threadIdx.x; c < n; c += blockDim.x)
-    sib[c] = beta1[c] > 0.0 ? (T)(1.0 / beta1[c]) : (T)0;
+__global__ void mr_finish_kernel(const T *__restrict__ zo, const T *__restrict__ wpp,
+                                 const T *__restrict__ wp, T *__restrict__ x,
+                                 const double *__restrict__ st, int n, long long L, FastDiv fd) {
+  __shared__ T cz[kMaxCols], ce[kMaxCols], cd[kMaxCols], cg[kMaxCols], ct[kMaxCols];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    cz[c] = (T)st[kMrIbp * n + c];
+    ce[c] = (T)st[kMrEps * n + c];
+    cd[c] = (T)st[kMrDel * n + c];
+    cg[c] = (T)st[kMrIg * n + c];
+    ct[c] = (T)st[kMrT * n + c];
+  }
   __syncthreads();
   GRID_STRIDE32(e, L * n) {
     const int c = (int)(e - fdiv(e, fd) * (uint32_t)n);
-    q[e] = b[e] * sib[c];
-    z[e] = zb[e] * sib[c];
+    const T w = (cz[c] * zo[e] - ce[c] * wpp[e] - cd[c] * wp[e]) * cg[c];
+    x[e] += ct[c] * w;
   }
 }
 
@@ -469,32 +517,32 @@ cudaError_t launch_scale_f32(const float *E, const double *, double alpha, int n
 }
 
 template <typename T>
-cudaError_t launch_mr_lanczos(const T *p, const T *q, const T *qprev, const double *alpha,
-                              const double *beta, const double *prec, int n, long long L, T *qhat,
-                              T *zhat, cudaStream_t s) {
+cudaError_t launch_mr_step(const T *ph, const T *qh, T *qo, T *zo, T *wpp, const T *wp, T *x,
+                           double *st, const double *prec, int n, long long L, cudaStream_t s) {
   ::invdft::count_launch();
-  mr_lanczos_kernel<T><<<grid_for(L * n), 256, 0, s>>>(p, q, qprev, alpha, beta, prec, n, L, qhat,
-                                                       zhat, make_fastdiv(n));
+  if (sizeof(T) == 4 && n % 4 == 0) {
+    const int n4 = n / 4;
+    mr_step_vec4_kernel<<<grid_for(L * n4), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(ph), reinterpret_cast<const float4 *>(qh),
+        reinterpret_cast<float4 *>(qo), reinterpret_cast<float4 *>(zo),
+        reinterpret_cast<float4 *>(wpp), reinterpret_cast<const float4 *>(wp),
+        reinterpret_cast<float4 *>(x), st, prec, n, L, make_fastdiv(n4));
+    return cudaGetLastError();
+  }
+  mr_step_kernel<T><<<grid_for(L * n), 256, 0, s>>>(ph, qh, qo, zo, wpp, wp, x, st, prec, n, L,
+                                                    make_fastdiv(n));
   return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_mr_update(T *z, const T *zhat, T *qn, const T *qhat, T *wpp, const T *wp, T *x,
-                             const double *st, int n, long long L, cudaStream_t s) {
+cudaError_t launch_mr_finish(const T *zo, T *wpp, const T *wp, T *x, const double *st, int n,
+                             long long L, cudaStream_t s) {
   ::invdft::count_launch();
-  mr_update_kernel<T><<<grid_for(L * n), 256, 0, s>>>(z, zhat, qn, qhat, wpp, wp, x, st, n, L,
-                                                      make_fastdiv(n));
+  mr_finish_kernel<T><<<grid_for(L * n), 256, 0, s>>>(zo, wpp, wp, x, st, n, L, make_fastdiv(n));
   return cudaGetLastError();
 }
 cudaError_t launch_mr_givens(int n, double *st, cudaStream_t s) {
   ::invdft::count_launch();
   mr_givens_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, st);
-  return cudaGetLastError();
-}
-template <typename T>
-cudaError_t launch_mr_init(const T *b, const T *zb, const double *beta1, int n, long long L, T *q,
-                           T *z, cudaStream_t s) {
-  ::invdft::count_launch();
-  mr_init_kernel<T><<<grid_for(L * n), 256, 0, s>>>(b, zb, beta1, n, L, q, z, make_fastdiv(n));
   return cudaGetLastError();
 }
 template <typename T>
@@ -518,13 +566,11 @@ cudaError_t launch_add_convert(const TI *d, TO *p, long long n, cudaStream_t s) 
 }
 
 #define INST_MR(T)                                                                              \
-  template cudaError_t launch_mr_lanczos<T>(const T *, const T *, const T *, const double *,    \
-                                            const double *, const double *, int, long long, T *, \
-                                            T *, cudaStream_t);                                 \
-  template cudaError_t launch_mr_update<T>(T *, const T *, T *, const T *, T *, const T *, T *,  \
-                                           const double *, int, long long, cudaStream_t);       \
-  template cudaError_t launch_mr_init<T>(const T *, const T *, const double *, int, long long,  \
-                                         T *, T *, cudaStream_t);                               \
+  template cudaError_t launch_mr_step<T>(const T *, const T *, T *, T *, T *, const T *, T *,    \
+                                         double *, const double *, int, long long,               \
+                                         cudaStream_t);                                          \
+  template cudaError_t launch_mr_finish<T>(const T *, T *, const T *, T *, const double *, int,  \
+                                           long long, cudaStream_t);                             \
   template cudaError_t launch_prec_apply<T>(const T *, const double *, int, long long, T *,     \
                                             cudaStream_t);
 INST_MR(double)

@@ -31,9 +31,6 @@ constexpr size_t kScPk = 512 * (size_t)kMaxCols;    // Chebyshev p_k(theta) tabl
 inline void set_tc(HxArgs<double> &, bool) {}
 inline void set_tc(HxArgs<float> &a, bool on) { a.tc = on; }
 
-// per-column MINRES scalars, st[k * n + c]
-enum { kMrAlpha = 0, kMrBeta, kMrBnext, kMrCpp, kMrSpp, kMrCp, kMrSp, kMrPhibar, kMrBeta1,
-       kMrActive, kMrEps, kMrDel, kMrIg, kMrT, kMrIb, kMrRel, kMrTol, kMrIters, kMrCount };
 
 double wall_ms() {
   using namespace std::chrono;
@@ -145,8 +142,7 @@ invdft_status rayleigh_ritz(Ctx *c, cudaStream_t s) {
   const long long L = c->L;
   double *S = c->small, *Hs = c->small + kMaxGram * kMaxGram, *Cm = c->small + 2 * kMaxGram * kMaxGram;
   double *work = c->small + 3 * kMaxGram * kMaxGram;
-  CU(launch_gram(c->Y, n, c->Y, n, L, S, c->partial, s), "gram(S)");
-  CU(launch_gram(c->Y, n, c->HY, n, L, Hs, c->partial, s), "gram(H)");
+  CU(launch_gram_rr(c->Y, c->HY, n, L, S, Hs, c->partial, s), "gram(S, H)");
   CU(launch_rr_small(S, Hs, n, c->eps, Cm, c->status, work, s), "rr_small");
   int st = 0;
   TRY(fetch(c, c->status, sizeof(int), &st, s));
@@ -398,7 +394,6 @@ template <typename T>
 invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s,
                       const T *V = nullptr, double *dot = nullptr) {
   double *Cp = c->small + 4 * kMaxGram * kMaxGram;
-  const bool big = ((nv + 3) / 4) * ((no + 3) / 4) >= 128;
   if (sizeof(T) == 8) {
     if (nv <= 64 && no <= 64)
       CU((launch_stripe_gram<double, double>((const double *)Psi, nv, (const double *)Z, no, c->L,
@@ -410,20 +405,17 @@ invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s
     if (V) CU(launch_coldot((const double *)V, (const double *)Z, no, c->L, dot, c->partial, s), "coldot");
     return INVDFT_OK;
   }
-  if (nv > 64 || no > 64) {
+  if (nv > 64 || no > 64 || nv % 8 != 0 || no % 4 != 0) {
     CU(launch_gram_f32acc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
        "gram(deflate)");
     CU(launch_rotate_acc<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "rotate(deflate)");
     if (V) CU(launch_coldot_f32((const float *)V, (const float *)Z, no, c->L, dot, c->partial, s), "coldot");
     return INVDFT_OK;
   }
-  if (big)
-    CU(launch_deflate_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial,
-                               s), "gram(deflate)");
-  else
-    CU((launch_stripe_gram<float, float>((const float *)Psi, nv, (const float *)Z, no, c->L, Cp,
-                                         c->partial, s)), "gram(deflate)");
-  if (no >= 32) {
+  // padded FP32 blocks (Psi width a multiple of 8, Z width of 4)
+  CU(launch_defl_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
+     "gram(deflate)");
+  if (no >= 16) {
     CU(launch_defl_update_f32((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
                               (const float *)V, dot, c->partial, s), "update(deflate)");
   } else {
@@ -438,21 +430,21 @@ invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s
 // every column at once, Q = I - Psi Psi^T, preconditioner Q T Q with T the
 // inverse diagonal of the kinetic part (Sec. 3.2.2).  b must lie in range(Q).
 template <typename T>
-invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, const T *b, T *x,
-                           const std::vector<double> &tol, int maxit, int *iters_out,
+invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int nv, const T *b,
+                           T *x, const std::vector<double> &tol, int maxit, int *iters_out,
                            cudaStream_t s) {
-  const int n = pl.no;
   const long long L = c->L;
   const size_t blk = (size_t)L * n;
-  T *qprev = (T *)c->mr[0], *q = (T *)c->mr[1], *z = (T *)c->mr[2], *wpp = (T *)c->mr[3];
-  T *wp = (T *)c->mr[4], *p = (T *)c->mr[5], *zh = (T *)c->mr[6];
+  // unnormalised Lanczos vectors qh, zh (current c, other o), w pair, H~ zh
+  T *qc = (T *)c->mr[0], *qo = (T *)c->mr[1], *zc = (T *)c->mr[2], *zo = (T *)c->mr[3];
+  T *wpp = (T *)c->mr[4], *wp = (T *)c->mr[5], *p = (T *)c->mr[6];
   double *st = c->scal + kScMr;    // kMrCount x n scalars
-  CU(launch_prec_apply<T>(b, c->prec_diag, n, L, z, s), "prec");
-  TRY(deflate<T>(c, Psi, nv, z, n, s));
+  CU(launch_prec_apply<T>(b, c->prec_diag, n, L, zc, s), "prec");
+  TRY(deflate<T>(c, Psi, nv, zc, n, s));
   if (sizeof(T) == 8)
-    CU(launch_coldot((const double *)b, (const double *)z, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
+    CU(launch_coldot((const double *)b, (const double *)zc, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
   else
-    CU(launch_coldot_f32((const float *)b, (const float *)z, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
+    CU(launch_coldot_f32((const float *)b, (const float *)zc, n, L, st + kMrBeta1 * n, c->partial, s), "coldot");
   std::vector<double> h((size_t)kMrCount * n, 0.0);
   TRY(fetch(c, st + kMrBeta1 * n, n * sizeof(double), h.data() + kMrBeta1 * n, s));
   for (int j = 0; j < n; ++j) {
@@ -464,10 +456,12 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, cons
     h[kMrCp * n + j] = 1.0;
     h[kMrTol * n + j] = tol[j];
     h[kMrRel * n + j] = b1 > 0.0 ? 1.0 : 0.0;
+    h[kMrIb * n + j] = b1 > 0.0 ? 1.0 / b1 : 0.0;     // q_0 = b / beta_1, z_0 = zh_0 / beta_1
   }
   TRY(push(c, st, h.data(), h.size() * sizeof(double), s));
-  CU(launch_mr_init<T>(b, z, st + kMrBeta1 * n, n, L, q, z, s), "mr_init");
-  CU(cudaMemsetAsync(qprev, 0, blk * sizeof(T), s), "memset");
+  CU(cudaMemcpyAsync(qc, b, blk * sizeof(T), cudaMemcpyDeviceToDevice, s), "copy");
+  CU(cudaMemsetAsync(qo, 0, blk * sizeof(T), s), "memset");
+  CU(cudaMemsetAsync(zo, 0, blk * sizeof(T), s), "memset");
   CU(cudaMemsetAsync(wpp, 0, blk * sizeof(T), s), "memset");
   CU(cudaMemsetAsync(wp, 0, blk * sizeof(T), s), "memset");
   CU(cudaMemsetAsync(x, 0, blk * sizeof(T), s), "memset");
@@ -485,22 +479,23 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, const T *Psi, int nv, cons
     // operands (relative error ~3e-4) the inner solves stall early and the
     // FP64 refinement needs several times more outer passes
     set_tc(a, false);
-    a.X = z;
+    a.X = zc;
     a.Z = p;
     a.ncol = n;
     a.shift_col = pl.d_eps_o;
     CU(hx_op(c, a, s), "hx(minres)");
-    // p <- Q p, alpha = z . p
-    TRY(deflate<T>(c, Psi, nv, p, n, s, z, st + kMrAlpha * n));
-    CU(launch_mr_lanczos<T>(p, q, qprev, st + kMrAlpha * n, st + kMrBeta * n, c->prec_diag, n, L,
-                            p, zh, s), "mr_lanczos");
-    // zhat <- Q zhat, beta_next^2 = qhat . zhat
-    TRY(deflate<T>(c, Psi, nv, zh, n, s, p, st + kMrBnext * n));
+    // p <- Q p, raw alpha = zh . p
+    TRY(deflate<T>(c, Psi, nv, p, n, s, zc, st + kMrRaw * n));
+    // qh_(k+1), zh_(k+1) = T qh_(k+1) (into qo, zo), pending solution update
+    CU(launch_mr_step<T>(p, qc, qo, zo, wpp, wp, x, st, c->prec_diag, n, L, s), "mr_step");
+    // zh <- Q zh, beta_(k+1)^2 = qh . zh
+    TRY(deflate<T>(c, Psi, nv, zo, n, s, qo, st + kMrBnext * n));
     CU(launch_mr_givens(n, st, s), "mr_givens");
-    CU(launch_mr_update<T>(z, zh, qprev, p, wpp, wp, x, st, n, L, s), "mr_update");
-    std::swap(qprev, q);
+    std::swap(qc, qo);
+    std::swap(zc, zo);
     std::swap(wpp, wp);
   }
+  CU(launch_mr_finish<T>(zo, wpp, wp, x, st, n, L, s), "mr_finish");
   std::vector<double> itv(n);
   TRY(fetch(c, st + kMrIters * n, n * sizeof(double), itv.data(), s));
   int mx = 0;
@@ -581,12 +576,13 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   double *dbase = c->scal + kScAdj;
   pl.d_eps_o = dbase;
   pl.d_f_o = dbase + kMaxDense;
-  std::vector<double> eo(no), fo(no);
-  for (int k = 0; k < no; ++k) {
-    eo[k] = eps[pl.idx[k]];
-    fo[k] = f[pl.idx[k]];
-  }
-  TRY(push(c, pl.d_eps_o, eo.data(), no * sizeof(double), s));
+  // the FP32 MINRES blocks are padded to a multiple of 4 columns with zero
+  // (inactive) columns; their shifts repeat the last real one
+  const int nop = (no + 3) / 4 * 4;
+  std::vector<double> eo(nop), fo(no);
+  for (int k = 0; k < nop; ++k) eo[k] = eps[pl.idx[std::min(k, no - 1)]];
+  for (int k = 0; k < no; ++k) fo[k] = f[pl.idx[k]];
+  TRY(push(c, pl.d_eps_o, eo.data(), nop * sizeof(double), s));
   TRY(push(c, pl.d_f_o, fo.data(), no * sizeof(double), s));
   // Psi_o (HY), b = 4 f omega psi (Rg), W = omega psi (Y); Psi_D (C1, FP64)
   double *Psi_o = c->HY, *R = c->Rg, *Wo = c->Y, *Po = c->P, *r64 = c->Y;
@@ -639,7 +635,8 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
   CU(cudaMemcpyAsync(r64, R, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
   const bool mixed = c->o.prec != INVDFT_FP64;
   float *Psi32 = (float *)c->C0;
-  if (mixed) CU(launch_convert_f64_to_f32(PsiD, Psi32, (long long)L * nd, s), "convert(psi)");
+  const int ndp = (nd + 7) / 8 * 8;
+  if (mixed) CU(launch_convert_pad_f32(PsiD, nd, ndp, L, Psi32, s), "convert(psi)");
   std::vector<double> rn(no), tol(no);
   int total_iters = 0, outer = 0;
   double relmax = 0.0;
@@ -670,13 +667,17 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
     int its = 0;
     if (mixed) {
       float *b32 = (float *)c->mr[8], *x32 = (float *)c->mr[7];
-      CU(launch_convert_f64_to_f32(r64, b32, (long long)blk, s), "convert");
-      TRY(minres_block<float>(c, pl, Psi32, nd, b32, x32, tol, c->o.max_minres_iters, &its, s));
-      CU((launch_add_convert<float, double>(x32, Po, (long long)blk, s)), "add");
+      CU(launch_convert_pad_f32(r64, no, nop, L, b32, s), "convert");
+      std::vector<double> tolp(nop, 1.0);
+      std::copy(tol.begin(), tol.end(), tolp.begin());
+      TRY(minres_block<float>(c, pl, nop, Psi32, ndp, b32, x32, tolp, c->o.max_minres_iters,
+                              &its, s));
+      CU(launch_add_unpad(x32, nop, Po, no, L, s), "add");
     } else {
       double *b64 = (double *)c->mr[8], *x64 = (double *)c->mr[7];
       CU(cudaMemcpyAsync(b64, r64, blk * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
-      TRY(minres_block<double>(c, pl, PsiD, nd, b64, x64, tol, c->o.max_minres_iters, &its, s));
+      TRY(minres_block<double>(c, pl, no, PsiD, nd, b64, x64, tol, c->o.max_minres_iters, &its,
+                               s));
       CU((launch_add_convert<double, double>(x64, Po, (long long)blk, s)), "add");
     }
     total_iters += its;
@@ -749,6 +750,7 @@ invdft_status loss_only(Ctx *c, const double *rd, const double *w, invdft_stats 
 
 invdft_status set_v(Ctx *c, const double *vxc, cudaStream_t s) {
   CU(launch_lincomb(1.0, c->vfixed, 1.0, vxc, c->v, c->L, s), "set_v");
+  CU(launch_convert_f64_to_f32(c->v, c->vf, c->L, s), "set_v(f32)");
   c->have_forward = false;
   c->have_upper = false;
   return INVDFT_OK;

@@ -53,19 +53,29 @@ cudaError_t launch_cheb_combine(const double *X, const double *pm, const float *
 cudaError_t launch_scale_f32(const float *E, const double *scale_scalar, double alpha, int n,
                              long long L, float *D, cudaStream_t s);
 
-// ---- MINRES elementwise steps (templated on the inner precision)
+// ---- MINRES (templated on the inner precision)
+// Per-column scalars st[k * n + c] of the batched MINRES recurrence.  The
+// Lanczos vectors are kept unnormalised (q_k = s_k qh_k, z_k = s_k zh_k with
+// s_k = 1 / beta_k): kMrIb holds s_k, kMrIbp s_(k-1), kMrRaw the dot
+// zh_k . (H~ - eps) zh_k, kMrAlpha alpha_k; kMrEps/Del/Ig/T are the Givens
+// coefficients of the solution update of the last finished iteration.
+enum { kMrAlpha = 0, kMrBeta, kMrBnext, kMrCpp, kMrSpp, kMrCp, kMrSp, kMrPhibar, kMrBeta1,
+       kMrActive, kMrEps, kMrDel, kMrIg, kMrT, kMrIb, kMrRel, kMrTol, kMrIters, kMrIbp, kMrRaw,
+       kMrCount };
+// One fused pass of iteration k (all [L][n] blocks, in place where noted):
+//   qh_(k+1) = s_k ph - alpha_k s_k qh_k - beta_k s_(k-1) qh_(k-1)   -> qo
+//   zh_(k+1) = T qh_(k+1)                                           -> zo
+//   w = (s_(k-1) zh_(k-1) - eps wpp - del wp) ig,  x += t w           -> wpp, x
+// with alpha_k = s_k^2 raw_k (also stored to kMrAlpha), qo holding qh_(k-1)
+// and zo holding zh_(k-1) on entry.  Inactive columns get qh = zh = 0.
 template <typename T>
-cudaError_t launch_mr_lanczos(const T *p, const T *q, const T *qprev, const double *alpha,
-                              const double *beta, const double *prec, int n, long long L, T *qhat,
-                              T *zhat, cudaStream_t s);
+cudaError_t launch_mr_step(const T *ph, const T *qh, T *qo, T *zo, T *wpp, const T *wp, T *x,
+                           double *st, const double *prec, int n, long long L, cudaStream_t s);
+// The solution update alone (after the last iteration): w and x as above.
 template <typename T>
-cudaError_t launch_mr_update(T *z, const T *zhat, T *qprev_to_qnext, const T *qhat, T *wpp,
-                             const T *wp, T *x, const double *coefs, int n, long long L,
-                             cudaStream_t s);
+cudaError_t launch_mr_finish(const T *zo, T *wpp, const T *wp, T *x, const double *st, int n,
+                             long long L, cudaStream_t s);
 cudaError_t launch_mr_givens(int n, double *st, cudaStream_t s);
-template <typename T>
-cudaError_t launch_mr_init(const T *b, const T *zb, const double *beta1, int n, long long L, T *q,
-                           T *z, cudaStream_t s);
 template <typename T>
 cudaError_t launch_prec_apply(const T *r, const double *prec, int n, long long L, T *z,
                               cudaStream_t s);
