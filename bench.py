@@ -47,6 +47,13 @@ import workloads as W  # noqa: E402
 
 METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 
+# DRAM bytes per (node, column) of one FP32 CUDA-core H~X launch: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of hx_simt_kernel<64, 0> on the
+# 24^3-cell Q4 mesh (857,375 unknowns) with 60 columns, 415.09 + 158.12 MB,
+# plus the 4-byte zero fill of Z that precedes the kernel in the same launch.
+# Traffic grows with unknowns x columns, so the in-step figure scales by them.
+HX_SIMT_DRAM_BYTES_PER_NODE_COL = (415.09e6 + 158.12e6) / (857375 * 60) + 4.0
+
 # H~X column-applications per inverse iteration on each workload, as counted by
 # the GPU path (line-search solves, Chebyshev passes, MINRES iterations) over the
 # timed steps of a mixed-precision run (cube32_q4_e100: 32,829 on average over
@@ -333,17 +340,25 @@ def run_ours(args, rank, world):
         return
     hx = None if args.no_hx else hx_benchmark(device)
     pk = peaks()
-    k32 = prof["fp32"] if prof["fp32"]["launches"] > 0 else prof["fp64"]
+    simt = prof["fp32"]["launches"] > 0
+    k32 = prof["fp32"] if simt else prof["fp64"]
+    nl = max(1, k32["launches"])
     achieved = k32["bytes"] / (k32["ms"] * 1e6) if k32["ms"] > 0 else None
     peak_gbs = pk["hbm_gbs"] if pk else 6400.0
     ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
-    col_applies = (prof["fp32"]["flops"] + prof["fp64"]["flops"]) / (2.0 * ne * ne * cells)
+    col_applies = sum(prof[k]["flops"] for k in ("fp64", "fp32", "tf32")) / (2.0 * ne * ne * cells)
+    bytes_per_launch = k32["bytes"] / nl
+    traffic = None
+    if simt:
+        ncol_avg = (bytes_per_launch / pb.L - 4.0) / 8.0
+        traffic = HX_SIMT_DRAM_BYTES_PER_NODE_COL * pb.L * ncol_avg
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-            "frac": (achieved / peak_gbs) if achieved else None, "traffic": None,
-            "kernel": "H~X (FP32 storage) inside the timed steps",
-            "launches": int(k32["launches"]), "avg_launch_ms": k32["ms"] / max(1, k32["launches"]),
+            "frac": (achieved / peak_gbs) if achieved else None, "traffic": traffic,
+            "kernel": ("hx_simt_kernel: FP32 H~X of the MINRES iterations (CUDA cores)" if simt
+                       else "hx_cells + hx_nodal: FP64 H~X"),
+            "launches": int(k32["launches"]), "avg_launch_ms": k32["ms"] / nl,
             "peak_source": "measured" if pk else "fallback",
-            "algorithmic_bytes_per_launch": k32["bytes"] / max(1, k32["launches"])}
+            "algorithmic_bytes_per_launch": bytes_per_launch}
     cpu = None
     if not args.no_cpu:
         cpu = oracle_baseline(wl, col_applies / args.steps)
@@ -364,10 +379,11 @@ def run_ours(args, rank, world):
                        "minres_iters": [s["minres_iters_max"] for s in stats],
                        "ls_trials": [s["ls_trials"] for s in stats],
                        "col_applies_per_step": col_applies / args.steps,
-                       "hx_ms_share": (prof["fp32"]["ms"] + prof["fp64"]["ms"])
+                       "hx_ms_share": sum(prof[k]["ms"] for k in ("fp64", "fp32", "tf32"))
                        / (ms_max * args.steps),
                        "hx_fp64_ms_per_step": prof["fp64"]["ms"] / args.steps,
-                       "hx_fp32_ms_per_step": prof["fp32"]["ms"] / args.steps},
+                       "hx_fp32_ms_per_step": prof["fp32"]["ms"] / args.steps,
+                       "hx_tf32_ms_per_step": prof["tf32"]["ms"] / args.steps},
     }
     print(json.dumps(line), flush=True)
     if world > 1:

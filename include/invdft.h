@@ -65,13 +65,13 @@ typedef enum {
 
 typedef enum {
   INVDFT_FP64 = 0,      /* every step in FP64                                     */
-  INVDFT_MIXED = 1,     /* FP32 storage, TF32 tensor-core cell products with FP32
-                           accumulation (Q4 meshes; FP32 CUDA cores for Q2) in
-                           the Chebyshev filter and the inner MINRES
+  INVDFT_MIXED = 1,     /* FP32 storage and FP32 cell products on the CUDA cores
+                           in the Chebyshev filter and the inner MINRES
                            iterations; FP64 for Rayleigh-Ritz, Cholesky,
                            residuals, refinement and every reduction             */
-  INVDFT_FP32 = 2       /* as MIXED but the FP32 cell products run on the CUDA
-                           cores in FP32 (no TF32 rounding)                      */
+  INVDFT_MIXED_TF32 = 2 /* as MIXED, but the Chebyshev filter's cell products
+                           (Q4 meshes) run on the TF32 tensor cores (tcgen05)
+                           with FP32 accumulation; MINRES stays in FP32         */
 } invdft_precision;
 
 /* Mesh: box [lo,hi]^3, ncell cells per axis, element order (2 or 4). */
@@ -98,7 +98,7 @@ typedef struct {
   int max_cheb_passes;    /* cap on filter + Rayleigh-Ritz passes       [60]   */
   int max_minres_iters;   /* cap on inner MINRES iterations per solve   [2000] */
   int lbfgs_history;      /* L-BFGS pairs kept                          [10]   */
-  invdft_precision prec;  /* FP64 or MIXED                                      */
+  invdft_precision prec;  /* FP64, MIXED or MIXED_TF32                          */
   unsigned long long seed;/* seed of the random start block                     */
   double deg_tol;         /* eigenvalues closer than this form a degenerate
                              set (Ha)                                   [1e-8] */
@@ -142,9 +142,9 @@ invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed_dev,
                                    const double *v_xc_dev, void *stream);
 
 /* Y = H~ X for an [L][ncol] block (Eq. 19, Sec. 3.2.3), device pointers.
- * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED (TF32 tensor cores on
- * Q4 meshes) or INVDFT_FP32 (FP32 CUDA cores): X, Y are float.  Y must not
- * alias X.
+ * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED (FP32 on the CUDA
+ * cores) or INVDFT_MIXED_TF32 (TF32 tensor cores on Q4 meshes): X, Y are
+ * float.  Y must not alias X.
  * ncol in [1, 256].  The operator used is the one of the last
  * invdft_set_potential.                                                     */
 invdft_status invdft_apply_h(invdft_handle h, const void *X_dev, void *Y_dev, int ncol,
@@ -201,14 +201,16 @@ invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const dou
 /* Instrumentation for benchmarks (no counterpart in the paper).
  * invdft_profile_hx: while enabled, every H~X launch of this handle is
  * bracketed by CUDA events on its stream.  Each call first drains pending
- * events (synchronising on them) and, if out8 != NULL, writes the totals
- * since the last enable: out8[0..3] = FP64 {device ms, algorithmic bytes
+ * events (synchronising on them) and, if out12 != NULL, writes the totals
+ * since the last enable: out12[0..3] = FP64 {device ms, algorithmic bytes
  * (X and v read, Z written, plus W/E when present), nominal dense-cell
- * flops 2 (p+1)^6 ncol ncell^3, launches}, out8[4..7] the same for FP32.
+ * flops 2 (p+1)^6 ncol ncell^3, launches}, out12[4..7] the same for FP32
+ * blocks on the CUDA cores, out12[8..11] for FP32 blocks on the TF32
+ * tensor-core kernel.
  * enable = 1 resets the totals and turns timing on; 0 turns it off.
  * invdft_kernel_launches: process-wide count of kernels launched by this
  * library since it was loaded.                                              */
-invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out8);
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12);
 invdft_status invdft_kernel_launches(unsigned long long *count);
 
 /* Allocation-free loss reduction.  The paper has no counterpart: this entry

@@ -14,11 +14,11 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_MIXED, INVDFT_OK, InvdftError, MeshDesc,
-                   Opts, Stats, check, lib)
+from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_MIXED, INVDFT_MIXED_TF32, INVDFT_OK,
+                   InvdftError, MeshDesc, Opts, Stats, check, lib)
 
 __all__ = ["Problem", "KohnShamDensity", "MeshDesc", "Opts", "Stats", "InvdftError",
-           "INVDFT_FP64", "INVDFT_MIXED", "library_path"]
+           "INVDFT_FP64", "INVDFT_MIXED", "INVDFT_MIXED_TF32", "library_path"]
 
 
 def library_path() -> str:
@@ -88,7 +88,8 @@ def invdft_set_potential(h, v_fixed: torch.Tensor, v_xc: torch.Tensor | None):
 def invdft_apply_h(h, X: torch.Tensor, Y: torch.Tensor, tensor_cores: bool = True):
     """Y = H~ X.  float64 blocks run in FP64; float32 blocks on the TF32 tensor
     cores (Q4 meshes) or, with tensor_cores=False, in FP32 on the CUDA cores."""
-    prec = INVDFT_FP64 if X.dtype == torch.float64 else (INVDFT_MIXED if tensor_cores else 2)
+    prec = (INVDFT_FP64 if X.dtype == torch.float64
+            else (INVDFT_MIXED_TF32 if tensor_cores else INVDFT_MIXED))
     if X.dtype != Y.dtype or X.dtype not in (torch.float64, torch.float32):
         raise ValueError("apply_h: X and Y must both be float64 or both float32")
     ncol = X.shape[1] if X.dim() == 2 else 1
@@ -144,11 +145,12 @@ def invdft_reset(h):
 
 
 def invdft_profile_hx(h, enable: bool):
-    out = np.zeros(8)
+    out = np.zeros(12)
     _ok("invdft_profile_hx", lib.invdft_profile_hx(h, int(enable), out.ctypes.data_as(C.c_void_p)),
         h, False)
     keys = ("ms", "bytes", "flops", "launches")
-    return {"fp64": dict(zip(keys, out[:4])), "fp32": dict(zip(keys, out[4:]))}
+    return {"fp64": dict(zip(keys, out[:4])), "fp32": dict(zip(keys, out[4:8])),
+            "tf32": dict(zip(keys, out[8:]))}
 
 
 def invdft_kernel_launches() -> int:
@@ -160,7 +162,12 @@ def invdft_kernel_launches() -> int:
 # ----------------------------------------------------------- owning wrapper
 
 class Problem:
-    """One inverse-DFT problem: a handle plus its torch-allocated workspace."""
+    """One inverse-DFT problem: a handle plus its torch-allocated workspace.
+
+    prec: "fp64" (every step in FP64), "mixed" (FP32 storage and FP32 cell
+    products on the CUDA cores in the Chebyshev filter and the inner MINRES,
+    FP64 elsewhere) or "tf32" (as "mixed", with the filter's Q4 cell products
+    on the TF32 tensor cores)."""
 
     def __init__(self, lo, hi, ncell, order, nstates, n_electrons=0.0, kT=0.0,
                  prec="fp64", cheb_degree=0, eig_tol=0.0, adj_tol=0.0, tau_bc=0.0,
@@ -173,7 +180,7 @@ class Problem:
                     eig_tol=float(eig_tol), adj_tol=float(adj_tol),
                     max_cheb_passes=int(max_cheb_passes), max_minres_iters=int(max_minres_iters),
                     lbfgs_history=int(lbfgs_history),
-                    prec={"mixed": INVDFT_MIXED, "fp32": 2}.get(prec, INVDFT_FP64),
+                    prec={"mixed": INVDFT_MIXED, "tf32": INVDFT_MIXED_TF32}.get(prec, INVDFT_FP64),
                     seed=int(seed),
                     deg_tol=float(deg_tol))
         self.h, self.L = invdft_create_mesh(mesh, opts)

@@ -326,7 +326,7 @@ invdft_status invdft_apply_h(invdft_handle h, const void *X, void *Y, int ncol,
     a.X = (const float *)X;
     a.Z = (float *)Y;
     a.ncol = ncol;
-    a.tc = prec == INVDFT_MIXED;
+    a.tc = prec == INVDFT_MIXED_TF32;
     e = hx_op(h, a, s);
   }
   if (!cuda_ok(h, e, "apply_h")) return INVDFT_ECUDA;
@@ -357,20 +357,20 @@ invdft_status invdft_reset(invdft_handle h) {
   return INVDFT_OK;
 }
 
-invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out8) {
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12) {
   if (!h) return INVDFT_EINVAL;
   HxProf &p = h->prof;
   if (!cuda_ok(h, prof_flush(h), "profile flush")) return INVDFT_ECUDA;
-  if (out8) {
-    for (int t = 0; t < 2; ++t) {
-      out8[4 * t + 0] = p.ms[t];
-      out8[4 * t + 1] = p.bytes_sum[t];
-      out8[4 * t + 2] = p.flops_sum[t];
-      out8[4 * t + 3] = (double)p.n[t];
+  if (out12) {
+    for (int t = 0; t < 3; ++t) {
+      out12[4 * t + 0] = p.ms[t];
+      out12[4 * t + 1] = p.bytes_sum[t];
+      out12[4 * t + 2] = p.flops_sum[t];
+      out12[4 * t + 3] = (double)p.n[t];
     }
   }
   if (enable) {
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < 3; ++t) {
       p.ms[t] = p.bytes_sum[t] = p.flops_sum[t] = 0.0;
       p.n[t] = 0;
     }

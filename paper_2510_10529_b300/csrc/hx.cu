@@ -287,16 +287,21 @@ namespace {
 // route an FP32 block to the tensor-core kernel when the mesh is Q4, the
 // caller asked for it and the output does not alias an input (the kernel
 // zeroes Z before accumulating into it)
+bool uses_tc(const Ctx *c, const HxArgs<double> &) { return false; }
+bool uses_tc(const Ctx *c, const HxArgs<float> &a) {
+  return a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
+         (const void *)a.Z != (const void *)a.E;
+}
+
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
   return launch_hx(c->g, c->v, a, s);
 }
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
-  const bool tc = a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
-                  (const void *)a.Z != (const void *)a.E;
+  const bool tc = uses_tc(c, a);
   if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + 8, s);
-  const bool simt_q4 = c->g.p == 4 && c->cell_perm && a.Z != a.X && a.Z != a.W &&
-                       (const void *)a.Z != (const void *)a.E;
-  if (simt_q4) return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, s);
+  const bool simt_q4 = c->g.p == 4 && c->cell_perm && a.ncol % 4 == 0 && a.Z != a.X &&
+                       a.Z != a.W && (const void *)a.Z != (const void *)a.E;
+  if (simt_q4) return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, c->status + 9, s);
   return launch_hx(c->g, c->v, a, s);
 }
 
@@ -321,12 +326,14 @@ cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   }
   const int k = p.used++;
   const double L = (double)c->L, n = a.ncol, sz = sizeof(T);
-  double bytes = (2.0 * n * sz + 8.0) * L;            // X read, Z written, v read
+  const int kind = sizeof(T) == 8 ? 0 : (uses_tc(c, a) ? 2 : 1);
+  // X read, Z written, v read (FP32 copy on the CUDA-core FP32 path)
+  double bytes = (2.0 * n * sz + (kind == 1 ? 4.0 : 8.0)) * L;
   if (a.W) bytes += n * sz * L;
   if (a.E) bytes += n * 4.0 * L;
   const double ne = (double)c->g.q * c->g.q * c->g.q;
   const double cells = (double)c->g.ncell * c->g.ncell * c->g.ncell;
-  p.kind[k] = sizeof(T) == 8 ? 0 : 1;
+  p.kind[k] = kind;
   p.bytes[k] = bytes;
   p.flops[k] = 2.0 * ne * ne * n * cells;
   cudaEventRecord(p.ev[2 * k], s);

@@ -1,16 +1,27 @@
 // FP32 H~X on the CUDA cores for Q4 cells: the exact-FP32 operator of the
-// inner MINRES iterations (the tensor-core TF32 kernel in hx_tc.cu is used by
-// the Chebyshev filter).  Same contract as the tensor-core kernel: the
-// launcher zeroes Z, every (cell, column chunk) tile gathers d o X_e with
-// float4 loads, applies K_e in its Kronecker-factored form (seven 1D
-// contractions of the 5x5x5 cell tensor in shared memory), and the epilogue
-// adds the nodal term for the nodes the cell owns and scatter-adds with
-// vector reductions.  In each contraction phase a thread owns one 1D line of
-// the cell for four adjacent columns (float4 shared-memory traffic), and the
-// 5x5 element matrices are kernel parameters, so they enter the FMAs as
-// constant operands.  Persistent CTAs walk the cells in the slab order of the
-// tensor-core kernel.
+// inner MINRES iterations and of the FP32 Chebyshev filter (the TF32
+// tensor-core kernel in hx_tc.cu is the alternative for the filter).
+//
+// Persistent CTAs walk the cells in the slab order of the tensor-core kernel.
+// For each (cell, chunk of C columns):
+//   * one thread fetches the 5x5x5 x C brick of X with a single 4D TMA tiled
+//     load (the unknowns form an Ni^3 grid of node rows, so a cell is a box
+//     of that grid; coordinates outside it read as zero, which is the
+//     Dirichlet boundary) into a staging buffer, one cell ahead;
+//   * K_e = kc (B(x)B(x)A + B(x)A(x)B + A(x)B(x)B) is applied as seven 1D
+//     contractions of the cell tensor in shared memory; in each phase a
+//     thread owns one 1D line for four adjacent columns, and the 5x5 element
+//     matrices (split into even / odd halves, they are centrosymmetric) are
+//     kernel parameters that enter the FMAs as constant operands;
+//   * the thread of x-line (y, z) scatter-adds that line's five nodes with
+//     vector reductions into Z (zeroed by the launcher), adding the nodal
+//     term alpha (v - shift) X (+ beta W + alpha escale E) for the nodes the
+//     cell owns (local index < 4 on every axis) from the raw X it read.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <mutex>
 
 #include "internal.h"
 
@@ -18,18 +29,20 @@ namespace invdft {
 namespace {
 
 constexpr int kQ = 5, kNe = 125;
+constexpr long long kSpinLimit = 1LL << 28;   // bounded mbarrier wait
 
 struct SmArgs {
-  const float *X;
   float *Z;
+  const float *X;           // for the W / E nodal terms' addressing only
   const float *W;
   const float *E;           // optional defect block, added as alpha escale_j E
   const double *escale;
-  const float *v;            // potential (FP32 copy)
+  const float *v;           // potential (FP32 copy)
   const double *shift_col;
   const float *dm1f;
   const int *perm;
-  // even / odd blocks of the centrosymmetric 1D matrices (see eo_apply)
+  int *err;                 // set to 2 when a wait for a TMA brick gives up
+  // even / odd blocks of the centrosymmetric 1D matrices (see eo_acc4)
   float eA[9], oA[4], eB[9], oB[4];
   float kc_alpha, alpha, beta, shift;
   int ncol, ncell, Ni;
@@ -61,224 +74,250 @@ __device__ __forceinline__ void eo_split4(const float4 *u, float4 *e, float4 *o)
   o[0] = f4_sub(u[0], u[4]);
   o[1] = f4_sub(u[1], u[3]);
 }
-// y = M1 u1 (+ M2 u2), each M given by its even (3x3) and odd (2x2) blocks
-template <bool TWO>
-__device__ __forceinline__ void eo_apply4(const float4 *e1, const float4 *o1, const float *eM1,
-                                          const float *oM1, const float4 *e2, const float4 *o2,
-                                          const float *eM2, const float *oM2, float4 *y) {
-  float4 ye[3], yo[2];
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
+  return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+// wait for phase `parity` of an mbarrier; false when the bounded wait gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  long long spins = 0;
+  while (!done) {
+    asm volatile(
+        "{\n .reg .pred pw;\n mbarrier.try_wait.parity.shared::cta.b64 pw, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, pw;\n}\n"
+        : "=r"(done) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    if (!done && ++spins > kSpinLimit) return false;
+  }
+  return true;
+}
+
+// y = M u for one or more lines u, accumulated on the even (3) and odd (2)
+// parts: ye, yo; streamed so that few values stay live.
+__device__ __forceinline__ void eo_acc4(const float4 *e, const float4 *o, const float *eM,
+                                        const float *oM, float4 *ye, float4 *yo, bool first) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 s = first ? make_float4(0.f, 0.f, 0.f, 0.f) : ye[i];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      s = f4_fma(eM1[i * 3 + k], e1[k], s);
-      if (TWO) s = f4_fma(eM2[i * 3 + k], e2[k], s);
-    }
+    for (int k = 0; k < 3; ++k) s = f4_fma(eM[i * 3 + k], e[k], s);
     ye[i] = s;
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 s = first ? make_float4(0.f, 0.f, 0.f, 0.f) : yo[i];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      s = f4_fma(oM1[i * 2 + k], o1[k], s);
-      if (TWO) s = f4_fma(oM2[i * 2 + k], o2[k], s);
-    }
+    for (int k = 0; k < 2; ++k) s = f4_fma(oM[i * 2 + k], o[k], s);
     yo[i] = s;
   }
-  y[0] = f4_add(ye[0], yo[0]);
-  y[4] = f4_sub(ye[0], yo[0]);
-  y[1] = f4_add(ye[1], yo[1]);
-  y[3] = f4_sub(ye[1], yo[1]);
-  y[2] = ye[2];
+}
+// y_i = ye_i + yo_i, y_(4-i) = ye_i - yo_i, y_2 = ye_2, stored at dst[i * stride]
+__device__ __forceinline__ void eo_store4(const float4 *ye, const float4 *yo, float4 *dst,
+                                          int stride) {
+  dst[0] = f4_add(ye[0], yo[0]);
+  dst[4 * stride] = f4_sub(ye[0], yo[0]);
+  dst[stride] = f4_add(ye[1], yo[1]);
+  dst[3 * stride] = f4_sub(ye[1], yo[1]);
+  dst[2 * stride] = ye[2];
 }
 
 template <int C, bool HW>
-__global__ void __launch_bounds__(simt_threads<C>(), 2) hx_simt_kernel(const __grid_constant__ SmArgs p) {
+__global__ void __launch_bounds__(simt_threads<C>(), 2)
+hx_simt_kernel(const __grid_constant__ SmArgs p, const __grid_constant__ CUtensorMap tmx) {
   constexpr int Q4 = C / 4;                  // column quads of a chunk
   constexpr int NT = 25 * Q4;                // tasks of a contraction phase
   constexpr int NTH = simt_threads<C>();
-  constexpr int NG = (kNe * Q4 + NTH - 1) / NTH;   // (node, quad) slots of a thread
-  extern __shared__ __align__(16) float4 sm4[];
-  float4 *u = sm4;                 // [125][Q4]
-  float4 *w = sm4 + kNe * Q4;      // [125][Q4]
-  __shared__ float dlf[3][5];
+  constexpr uint32_t kBrickBytes = kNe * C * 4;
+  extern __shared__ unsigned char sm_raw[];
+  // TMA destinations want 128-byte alignment
+  float4 *stg = reinterpret_cast<float4 *>(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
+  float4 *u = stg + kNe * Q4;      // [125][Q4]
+  float4 *w = u + kNe * Q4;        // [125][Q4]
+  __shared__ uint64_t mbar;
+  __shared__ float dlf[2][3][5];   // d = m^-1/2 along each axis, per staged cell
+  __shared__ int abort_flag;
   __shared__ float sshift[kMaxCols], sesc[kMaxCols];
   const int tid = threadIdx.x;
   const int nc = p.ncell, Ni = p.Ni, ncol = p.ncol;
-  const int ncells = nc * nc * nc;
   const int nchunk = (ncol + C - 1) / C;
-  const int items = ncells * nchunk;
+  const int items = nc * nc * nc * nchunk;
   for (int j = tid; j < ncol; j += NTH) {
     sshift[j] = (float)(p.shift_col ? p.shift_col[j] : p.shift);
     sesc[j] = p.E ? (float)(p.alpha * p.escale[j]) : 0.f;
   }
-  const bool vec = (ncol & 3) == 0;
-  const bool act = tid < NT;
-  const int q = tid % Q4, l = tid / Q4;      // this thread's task: line l, quad q
-  // The (node, quad) slots a thread gathers and scatters are the same for
-  // every cell: cell-local node offset, quad, and the bits that make a slot
-  // void on a boundary cell (1,2: x = 0 / 4; 4,8: y; 16,32: z), 64 = owned
-  // (local index < 4 on every axis), 128 = no slot.
-  int goff[NG], gq[NG], gflag[NG], gl[NG];
-#pragma unroll
-  for (int k = 0; k < NG; ++k) {
-    const int idx = tid + k * NTH;
-    const int a = idx / Q4, c4 = idx - (idx / Q4) * Q4;
-    const int lx = a % 5, ly = (a / 5) % 5, lz = a / 25;
-    goff[k] = lx + Ni * (ly + Ni * lz);
-    gq[k] = c4;
-    gl[k] = lx | (ly << 4) | (lz << 8);
-    gflag[k] = idx >= kNe * Q4 ? 128
-             : (lx == 0) | ((lx == 4) << 1) | ((ly == 0) << 2) | ((ly == 4) << 3) |
-                   ((lz == 0) << 4) | ((lz == 4) << 5) | ((lx < 4 && ly < 4 && lz < 4) << 6);
+  if (tid == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int chunk = item % nchunk;
+  const bool act = tid < NT;
+  const int q = tid % Q4, l = tid / Q4;      // this thread's line l = ly + 5 lz, quad q
+  const int ly = l % 5, lz = l / 5;
+  __syncthreads();
+  auto locate = [&](int item, int &c0, int &cx, int &cy, int &cz) {
     const int cell = p.perm[item / nchunk];
-    const int c0 = chunk * C;
-    const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
-    // void slots of this cell; node index of local (0, 0, 0)
-    const int edge = (cx == 0) | ((cx == nc - 1) << 1) | ((cy == 0) << 2) | ((cy == nc - 1) << 3) |
-                     ((cz == 0) << 4) | ((cz == nc - 1) << 5) | 128;
-    const int base = (4 * cx - 1) + Ni * ((4 * cy - 1) + Ni * (4 * cz - 1));
-    __syncthreads();
+    c0 = (item % nchunk) * C;
+    cx = cell % nc;
+    cy = (cell / nc) % nc;
+    cz = cell / (nc * nc);
+  };
+  // stage an item: d tables, the brick by TMA, and the potential of the
+  // nodes this thread owns on its x-line (into vn)
+  float vn[4] = {0.f, 0.f, 0.f, 0.f};
+  auto stage = [&](int item, int buf) {
+    int c0, cx, cy, cz;
+    locate(item, c0, cx, cy, cz);
     if (tid < 15) {
       const int d = tid / 5, t = tid % 5;
-      const int g = (d == 0 ? cx : (d == 1 ? cy : cz)) * 4 + t;
-      dlf[d][t] = p.dm1f[g];
+      dlf[buf][d][t] = p.dm1f[(d == 0 ? cx : (d == 1 ? cy : cz)) * 4 + t];
     }
-    __syncthreads();
-    // gather u[a][quad] = d_a X[node(a)][c0 + 4 quad ...]
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   :: "r"(smem_addr(&mbar)), "r"(kBrickBytes) : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+          " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+          :: "r"(smem_addr(stg)), "l"(&tmx), "r"(c0), "r"(4 * cx - 1), "r"(4 * cy - 1),
+             "r"(4 * cz - 1), "r"(smem_addr(&mbar))
+          : "memory");
+    }
+    const int gy = 4 * cy - 1 + ly, gz = 4 * cz - 1 + lz;
 #pragma unroll
-    for (int k = 0; k < NG; ++k) {
-      if (gflag[k] & 128) continue;
-      const int col = c0 + 4 * gq[k];
-      float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!(gflag[k] & edge) && col < ncol) {
-        const uint32_t e0 = (uint32_t)(base + goff[k]) * (uint32_t)ncol + (uint32_t)col;
-        const float sc = dlf[0][gl[k] & 15] * dlf[1][(gl[k] >> 4) & 15] * dlf[2][gl[k] >> 8];
-        const float *src = p.X + e0;
-        float4 x;
-        if (vec) {
-          x = __ldg(reinterpret_cast<const float4 *>(src));
-        } else {
-          x.x = __ldg(src);
-          x.y = col + 1 < ncol ? __ldg(src + 1) : 0.f;
-          x.z = col + 2 < ncol ? __ldg(src + 2) : 0.f;
-          x.w = col + 3 < ncol ? __ldg(src + 3) : 0.f;
-        }
-        v4 = make_float4(sc * x.x, sc * x.y, sc * x.z, sc * x.w);
-      }
-      u[tid + k * NTH] = v4;
+    for (int x = 0; x < 4; ++x) vn[x] = 0.f;
+    if (act && ly < 4 && lz < 4 && gy >= 0 && gz >= 0) {
+      const int row = Ni * (gy + Ni * gz) + 4 * cx - 1;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+        vn[x] = (4 * cx - 1 + x >= 0) ? __ldg(p.v + row + x) : 0.f;
     }
+  };
+  if ((int)blockIdx.x < items) stage(blockIdx.x, 0);
+  int it = 0;
+  for (int item = blockIdx.x; item < items; item += gridDim.x, ++it) {
+    const int buf = it & 1;
+    int c0, cx, cy, cz;
+    locate(item, c0, cx, cy, cz);
+    if (!mbar_wait(&mbar, (uint32_t)(it & 1))) abort_flag = 1;
     __syncthreads();
-    // x lines (nodes 5 l .. 5 l + 4): u <- B_x u, w <- A_x u
+    if (abort_flag) break;
+    float vc[4] = {vn[0], vn[1], vn[2], vn[3]};
+    // x lines (nodes 5 l .. 5 l + 4) from the raw brick, scaled by d:
+    // u <- B_x u, w <- A_x u; the nodal term of the owned nodes is kept
+    float4 nod[4];
     if (act) {
-      float4 in[kQ], e[3], o[2], yb[kQ], ya[kQ];
+      const float syz = dlf[buf][1][ly] * dlf[buf][2][lz];
+      float4 in[kQ], e[3], o[2];
 #pragma unroll
-      for (int x = 0; x < kQ; ++x) in[x] = u[(5 * l + x) * Q4 + q];
-      eo_split4(in, e, o);
-      eo_apply4<false>(e, o, p.eB, p.oB, e, o, p.eB, p.oB, yb);
-      eo_apply4<false>(e, o, p.eA, p.oA, e, o, p.eA, p.oA, ya);
-#pragma unroll
-      for (int xo = 0; xo < kQ; ++xo) {
-        u[(5 * l + xo) * Q4 + q] = yb[xo];
-        w[(5 * l + xo) * Q4 + q] = ya[xo];
+      for (int x = 0; x < kQ; ++x) {
+        const float4 r = stg[(5 * l + x) * Q4 + q];
+        const float sc = dlf[buf][0][x] * syz;
+        in[x] = make_float4(sc * r.x, sc * r.y, sc * r.z, sc * r.w);
+        if (x < 4) {
+          const int col = min(c0 + 4 * q, ncol - 4);
+          nod[x] = make_float4(p.alpha * (vc[x] - sshift[col]) * r.x,
+                               p.alpha * (vc[x] - sshift[col + 1]) * r.y,
+                               p.alpha * (vc[x] - sshift[col + 2]) * r.z,
+                               p.alpha * (vc[x] - sshift[col + 3]) * r.w);
+        }
       }
+      eo_split4(in, e, o);
+      float4 ye[3], yo[2];
+      eo_acc4(e, o, p.eB, p.oB, ye, yo, true);
+      eo_store4(ye, yo, u + 5 * l * Q4 + q, Q4);
+      eo_acc4(e, o, p.eA, p.oA, ye, yo, true);
+      eo_store4(ye, yo, w + 5 * l * Q4 + q, Q4);
     }
     __syncthreads();
+    // the staging buffer is free: fetch the next cell while this one finishes
+    if (item + (int)gridDim.x < items) stage(item + gridDim.x, buf ^ 1);
     // y lines (l = x + 5 z): u <- B_y u, w <- A_y u + B_y w
     if (act) {
-      const int base = (l % 5) + 25 * (l / 5);
-      float4 t[kQ], e1[3], o1[2], e2[3], o2[2], y1[kQ];
+      const int lb = (l % 5) + 25 * (l / 5);
+      float4 t[kQ], e[3], o[2], ye[3], yo[2];
 #pragma unroll
-      for (int y = 0; y < kQ; ++y) t[y] = u[(base + 5 * y) * Q4 + q];
-      eo_split4(t, e1, o1);
+      for (int y = 0; y < kQ; ++y) t[y] = u[(lb + 5 * y) * Q4 + q];
+      eo_split4(t, e, o);
+      eo_acc4(e, o, p.eB, p.oB, ye, yo, true);
+      eo_store4(ye, yo, u + lb * Q4 + q, 5 * Q4);
+      eo_acc4(e, o, p.eA, p.oA, ye, yo, true);
 #pragma unroll
-      for (int y = 0; y < kQ; ++y) t[y] = w[(base + 5 * y) * Q4 + q];
-      eo_split4(t, e2, o2);
-      eo_apply4<false>(e1, o1, p.eB, p.oB, e1, o1, p.eB, p.oB, y1);
-#pragma unroll
-      for (int yo = 0; yo < kQ; ++yo) u[(base + 5 * yo) * Q4 + q] = y1[yo];
-      eo_apply4<true>(e1, o1, p.eA, p.oA, e2, o2, p.eB, p.oB, y1);
-#pragma unroll
-      for (int yo = 0; yo < kQ; ++yo) w[(base + 5 * yo) * Q4 + q] = y1[yo];
+      for (int y = 0; y < kQ; ++y) t[y] = w[(lb + 5 * y) * Q4 + q];
+      eo_split4(t, e, o);
+      eo_acc4(e, o, p.eB, p.oB, ye, yo, false);
+      eo_store4(ye, yo, w + lb * Q4 + q, 5 * Q4);
     }
     __syncthreads();
     // z lines (l = x + 5 y): u <- A_z u + B_z w
     if (act) {
-      float4 t[kQ], e1[3], o1[2], e2[3], o2[2], yz[kQ];
+      float4 t[kQ], e[3], o[2], ye[3], yo[2];
 #pragma unroll
       for (int z = 0; z < kQ; ++z) t[z] = u[(l + 25 * z) * Q4 + q];
-      eo_split4(t, e1, o1);
+      eo_split4(t, e, o);
+      eo_acc4(e, o, p.eA, p.oA, ye, yo, true);
 #pragma unroll
       for (int z = 0; z < kQ; ++z) t[z] = w[(l + 25 * z) * Q4 + q];
-      eo_split4(t, e2, o2);
-      eo_apply4<true>(e1, o1, p.eA, p.oA, e2, o2, p.eB, p.oB, yz);
-#pragma unroll
-      for (int zo = 0; zo < kQ; ++zo) u[(l + 25 * zo) * Q4 + q] = yz[zo];
+      eo_split4(t, e, o);
+      eo_acc4(e, o, p.eB, p.oB, ye, yo, false);
+      eo_store4(ye, yo, u + l * Q4 + q, 25 * Q4);
     }
     __syncthreads();
-    // epilogue: the thread's (node, quad) slots; nodal term for owned nodes
+    // epilogue: the five nodes of this thread's x-line
+    if (act) {
+      const int gy = 4 * cy - 1 + ly, gz = 4 * cz - 1 + lz;
+      const int col = c0 + 4 * q;
+      if (gy >= 0 && gy < Ni && gz >= 0 && gz < Ni && col < ncol) {
+        const float syz = p.kc_alpha * dlf[buf][1][ly] * dlf[buf][2][lz];
+        const bool own_yz = ly < 4 && lz < 4;
+        const uint32_t row = (uint32_t)(Ni * (gy + Ni * gz) + 4 * cx - 1);
 #pragma unroll
-    for (int k = 0; k < NG; ++k) {
-      const int col = c0 + 4 * gq[k];
-      if ((gflag[k] & edge) || col >= ncol) continue;
-      const uint32_t node = (uint32_t)(base + goff[k]);
-      const uint32_t e0 = node * (uint32_t)ncol + (uint32_t)col;
-      const float sc =
-          p.kc_alpha * dlf[0][gl[k] & 15] * dlf[1][(gl[k] >> 4) & 15] * dlf[2][gl[k] >> 8];
-      const float4 y = u[tid + k * NTH];
-      float o[4] = {sc * y.x, sc * y.y, sc * y.z, sc * y.w};
-      const int m = min(4, ncol - col);
-      if (gflag[k] & 64) {
-        const float va = __ldg(p.v + node);
-        float xs[4] = {0.f, 0.f, 0.f, 0.f}, ws[4] = {0.f, 0.f, 0.f, 0.f};
-        float es[4] = {0.f, 0.f, 0.f, 0.f};
-        if (vec) {
-          const float4 x4 = __ldg(reinterpret_cast<const float4 *>(p.X + e0));
-          xs[0] = x4.x; xs[1] = x4.y; xs[2] = x4.z; xs[3] = x4.w;
-          if (HW) {
-            const float4 w4 = *reinterpret_cast<const float4 *>(p.W + e0);
-            ws[0] = w4.x; ws[1] = w4.y; ws[2] = w4.z; ws[3] = w4.w;
+        for (int x = 0; x < kQ; ++x) {
+          const int gx = 4 * cx - 1 + x;
+          if (gx < 0 || gx >= Ni) continue;
+          const uint32_t e0 = (row + x) * (uint32_t)ncol + (uint32_t)col;
+          const float sc = syz * dlf[buf][0][x];
+          const float4 y = u[(5 * l + x) * Q4 + q];
+          float4 o = make_float4(sc * y.x, sc * y.y, sc * y.z, sc * y.w);
+          if (x < 4 && own_yz) {
+            o.x += nod[x].x;
+            o.y += nod[x].y;
+            o.z += nod[x].z;
+            o.w += nod[x].w;
+            if (HW) {
+              const float4 w4 = *reinterpret_cast<const float4 *>(p.W + e0);
+              o.x = fmaf(p.beta, w4.x, o.x);
+              o.y = fmaf(p.beta, w4.y, o.y);
+              o.z = fmaf(p.beta, w4.z, o.z);
+              o.w = fmaf(p.beta, w4.w, o.w);
+            }
+            if (p.E) {
+              const float4 e4 = __ldg(reinterpret_cast<const float4 *>(p.E + e0));
+              o.x = fmaf(sesc[col], e4.x, o.x);
+              o.y = fmaf(sesc[col + 1], e4.y, o.y);
+              o.z = fmaf(sesc[col + 2], e4.z, o.z);
+              o.w = fmaf(sesc[col + 3], e4.w, o.w);
+            }
           }
-          if (p.E) {
-            const float4 e4 = __ldg(reinterpret_cast<const float4 *>(p.E + e0));
-            es[0] = e4.x; es[1] = e4.y; es[2] = e4.z; es[3] = e4.w;
-          }
-        } else {
-          for (int t = 0; t < m; ++t) {
-            xs[t] = p.X[e0 + t];
-            if (HW) ws[t] = p.W[e0 + t];
-            if (p.E) es[t] = p.E[e0 + t];
-          }
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int jc = min(col + t, ncol - 1);
-          float tt = p.alpha * (va - sshift[jc]) * xs[t];
-          if (HW) tt = fmaf(p.beta, ws[t], tt);
-          tt = fmaf(sesc[jc], es[t], tt);
-          o[t] += tt;
+          // no "memory" clobber: nothing in this kernel reads Z
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                       :: "l"(p.Z + e0), "f"(o.x), "f"(o.y), "f"(o.z), "f"(o.w));
         }
       }
-      float *dst = p.Z + e0;
-      if (vec) {
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
-                     :: "l"(dst), "f"(o[0]), "f"(o[1]), "f"(o[2]), "f"(o[3]) : "memory");
-      } else {
-        for (int t = 0; t < m; ++t)
-          asm volatile("red.global.add.f32 [%0], %1;" :: "l"(dst + t), "f"(o[t]) : "memory");
-      }
+    }
+  }
+  if (abort_flag) {
+    // a brick never arrived: report, and give a copy still in flight a
+    // bounded chance to land before the CTA's shared memory is released
+    if (tid == 0) {
+      atomicExch(p.err, 2);
+      mbar_wait(&mbar, (uint32_t)(it & 1));
     }
   }
 }
 
 template <int C, bool HW>
-cudaError_t run_simt(const SmArgs &p, long long items, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)kNe * C * sizeof(float);
+cudaError_t run_simt(const SmArgs &p, const CUtensorMap &tm, long long items, cudaStream_t s) {
+  const size_t smem = 3 * (size_t)kNe * C * sizeof(float) + 128;
   auto k = hx_simt_kernel<C, HW>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -288,22 +327,56 @@ cudaError_t run_simt(const SmArgs &p, long long items, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(items, (long long)nsm * std::max(per_sm, 1));
   ::invdft::count_launch();
-  k<<<grid, simt_threads<C>(), smem, s>>>(p);
+  k<<<grid, simt_threads<C>(), smem, s>>>(p, tm);
   return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime so that the library
+// loads on hosts without the driver (it is only called with a GPU present)
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
 }
 
 }  // namespace
 
-// FP32 CUDA-core H~X for Q4 meshes (W and E optional).  Z must not alias X,
-// W or E; it is zeroed here.
+// FP32 CUDA-core H~X for Q4 meshes (W and E optional), ncol a multiple of 4
+// (16-byte node rows for the TMA brick loads).  Z must not alias X, W or E;
+// it is zeroed here.  err: device word set to 2 if a brick load timed out.
 cudaError_t launch_hx_simt_q4(const Geom &g, const float *v, const HxArgs<float> &a,
-                              const int *perm, cudaStream_t s) {
-  if (g.p != 4) return cudaErrorInvalidValue;
+                              const int *perm, int *err, cudaStream_t s) {
+  if (g.p != 4 || a.ncol % 4 != 0 || a.ncol > kMaxCols) return cudaErrorInvalidValue;
+  if (((uintptr_t)a.X & 15) != 0) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(a.Z, 0, (size_t)g.L * a.ncol * sizeof(float), s);
   if (e != cudaSuccess) return e;
+  const int C = a.ncol <= 16 ? 16 : (a.ncol <= 32 ? 32 : 64);
+  // X as a 4D tensor (column, x, y, z) of the interior node grid; box = one
+  // cell's 5 x 5 x 5 nodes by C columns
+  CUtensorMap tm;
+  const cuuint64_t dims[4] = {(cuuint64_t)a.ncol, (cuuint64_t)g.Ni, (cuuint64_t)g.Ni,
+                              (cuuint64_t)g.Ni};
+  const cuuint64_t row = (cuuint64_t)a.ncol * sizeof(float);
+  const cuuint64_t strides[3] = {row, row * g.Ni, row * g.Ni * g.Ni};
+  const cuuint32_t box[4] = {(cuuint32_t)C, 5, 5, 5};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)a.X, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   SmArgs p;
-  p.X = a.X;
   p.Z = a.Z;
+  p.X = a.X;
   p.W = a.W;
   p.E = a.E;
   p.escale = a.escale;
@@ -311,16 +384,17 @@ cudaError_t launch_hx_simt_q4(const Geom &g, const float *v, const HxArgs<float>
   p.shift_col = a.shift_col;
   p.dm1f = g.dm1f;
   p.perm = perm;
+  p.err = err;
   // even / odd blocks of the (symmetrised) centrosymmetric 1D matrices
   for (int m = 0; m < 2; ++m) {
     const double *M = m == 0 ? g.A : g.B;
-    float *e = m == 0 ? p.eA : p.eB, *o = m == 0 ? p.oA : p.oB;
+    float *ev = m == 0 ? p.eA : p.eB, *ov = m == 0 ? p.oA : p.oB;
     auto sym = [&](int i, int j) { return 0.5 * (M[i * 5 + j] + M[(4 - i) * 5 + (4 - j)]); };
     for (int i = 0; i < 3; ++i)
       for (int k = 0; k < 3; ++k)
-        e[i * 3 + k] = (float)(k < 2 ? 0.5 * (sym(i, k) + sym(i, 4 - k)) : sym(i, 2));
+        ev[i * 3 + k] = (float)(k < 2 ? 0.5 * (sym(i, k) + sym(i, 4 - k)) : sym(i, 2));
     for (int i = 0; i < 2; ++i)
-      for (int k = 0; k < 2; ++k) o[i * 2 + k] = (float)(0.5 * (sym(i, k) - sym(i, 4 - k)));
+      for (int k = 0; k < 2; ++k) ov[i * 2 + k] = (float)(0.5 * (sym(i, k) - sym(i, 4 - k)));
   }
   p.kc_alpha = (float)(g.kc * a.alpha);
   p.alpha = (float)a.alpha;
@@ -329,11 +403,10 @@ cudaError_t launch_hx_simt_q4(const Geom &g, const float *v, const HxArgs<float>
   p.ncol = a.ncol;
   p.ncell = g.ncell;
   p.Ni = g.Ni;
-  const int C = a.ncol <= 16 ? 16 : (a.ncol <= 32 ? 32 : 64);
   const long long items = (long long)g.ncell * g.ncell * g.ncell * ((a.ncol + C - 1) / C);
-  if (C == 16) return a.W ? run_simt<16, true>(p, items, s) : run_simt<16, false>(p, items, s);
-  if (C == 32) return a.W ? run_simt<32, true>(p, items, s) : run_simt<32, false>(p, items, s);
-  return a.W ? run_simt<64, true>(p, items, s) : run_simt<64, false>(p, items, s);
+  if (C == 16) return a.W ? run_simt<16, true>(p, tm, items, s) : run_simt<16, false>(p, tm, items, s);
+  if (C == 32) return a.W ? run_simt<32, true>(p, tm, items, s) : run_simt<32, false>(p, tm, items, s);
+  return a.W ? run_simt<64, true>(p, tm, items, s) : run_simt<64, false>(p, tm, items, s);
 }
 
 }  // namespace invdft

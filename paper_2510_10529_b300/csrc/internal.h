@@ -64,8 +64,9 @@ struct HxProf {
   std::vector<int> kind;
   std::vector<double> bytes, flops;
   int used = 0;
-  double ms[2] = {0, 0}, bytes_sum[2] = {0, 0}, flops_sum[2] = {0, 0};
-  long long n[2] = {0, 0};
+  // kinds: 0 FP64, 1 FP32 on the CUDA cores, 2 TF32 on the tensor cores
+  double ms[3] = {0, 0, 0}, bytes_sum[3] = {0, 0, 0}, flops_sum[3] = {0, 0, 0};
+  long long n[3] = {0, 0, 0};
 };
 
 struct Ctx {
@@ -195,7 +196,7 @@ cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a,
                          const int *perm, int *err, cudaStream_t s);
 void build_cell_order(int nc, std::vector<int> *perm);
 cudaError_t launch_hx_simt_q4(const Geom &g, const float *vf, const HxArgs<float> &a,
-                              const int *perm, cudaStream_t s);
+                              const int *perm, int *err, cudaStream_t s);
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).

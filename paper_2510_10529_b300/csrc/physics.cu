@@ -303,7 +303,7 @@ __global__ void mr_step_vec4_kernel(const float4 *__restrict__ ph, const float4 
                                     float4 *__restrict__ qo, float4 *__restrict__ zo,
                                     float4 *__restrict__ wpp, const float4 *__restrict__ wp,
                                     float4 *__restrict__ x, double *__restrict__ st,
-                                    const double *__restrict__ prec, int n, long long L,
+                                    const float *__restrict__ prec, int n, long long L,
                                     FastDiv fd4) {
   __shared__ float4 c1[kMaxCols / 4], c2[kMaxCols / 4], c3[kMaxCols / 4], cz[kMaxCols / 4];
   __shared__ float4 ce[kMaxCols / 4], cd[kMaxCols / 4], cg[kMaxCols / 4], ct[kMaxCols / 4];
@@ -334,7 +334,7 @@ __global__ void mr_step_vec4_kernel(const float4 *__restrict__ ph, const float4 
     const float4 p0 = ph[e], q1 = qh[e], q0 = qo[e];
     const float4 a1 = c1[c], a2 = c2[c], a3 = c3[c], az = cz[c];
     const float4 ae = ce[c], ad = cd[c], ag = cg[c], at = ct[c];
-    const float pr = (float)prec[a];
+    const float pr = prec[a];
     float4 w, xn, q, z;
 #define MR_LANE(k)                                                      \
   w.k = (az.k * z0.k - ae.k * w2.k - ad.k * w1.k) * ag.k;               \
@@ -518,7 +518,8 @@ cudaError_t launch_scale_f32(const float *E, const double *, double alpha, int n
 
 template <typename T>
 cudaError_t launch_mr_step(const T *ph, const T *qh, T *qo, T *zo, T *wpp, const T *wp, T *x,
-                           double *st, const double *prec, int n, long long L, cudaStream_t s) {
+                           double *st, const double *prec, const float *precf, int n, long long L,
+                           cudaStream_t s) {
   ::invdft::count_launch();
   if (sizeof(T) == 4 && n % 4 == 0) {
     const int n4 = n / 4;
@@ -526,7 +527,7 @@ cudaError_t launch_mr_step(const T *ph, const T *qh, T *qo, T *zo, T *wpp, const
         reinterpret_cast<const float4 *>(ph), reinterpret_cast<const float4 *>(qh),
         reinterpret_cast<float4 *>(qo), reinterpret_cast<float4 *>(zo),
         reinterpret_cast<float4 *>(wpp), reinterpret_cast<const float4 *>(wp),
-        reinterpret_cast<float4 *>(x), st, prec, n, L, make_fastdiv(n4));
+        reinterpret_cast<float4 *>(x), st, precf, n, L, make_fastdiv(n4));
     return cudaGetLastError();
   }
   mr_step_kernel<T><<<grid_for(L * n), 256, 0, s>>>(ph, qh, qo, zo, wpp, wp, x, st, prec, n, L,
@@ -567,7 +568,7 @@ cudaError_t launch_add_convert(const TI *d, TO *p, long long n, cudaStream_t s) 
 
 #define INST_MR(T)                                                                              \
   template cudaError_t launch_mr_step<T>(const T *, const T *, T *, T *, T *, const T *, T *,    \
-                                         double *, const double *, int, long long,               \
+                                         double *, const double *, const float *, int, long long, \
                                          cudaStream_t);                                          \
   template cudaError_t launch_mr_finish<T>(const T *, T *, const T *, T *, const double *, int,  \
                                            long long, cudaStream_t);                             \

@@ -226,7 +226,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
         err = hx_op(c, h, s);
       } else {
         HxArgs<float> h;
-        h.tc = c->o.prec == INVDFT_MIXED;
+        h.tc = c->o.prec == INVDFT_MIXED_TF32;
         h.X = (const float *)cur;
         h.Z = (float *)Z;
         h.ncol = ncol;
@@ -274,7 +274,7 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
     const double sn = sig[k];
     void *Z = free_buf(prev, cur);
     HxArgs<float> h;
-    h.tc = c->o.prec == INVDFT_MIXED;
+    h.tc = c->o.prec == INVDFT_MIXED_TF32;
     h.X = (const float *)cur;
     h.Z = (float *)Z;
     h.ncol = ncol;
@@ -487,7 +487,8 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int n
     // p <- Q p, raw alpha = zh . p
     TRY(deflate<T>(c, Psi, nv, p, n, s, zc, st + kMrRaw * n));
     // qh_(k+1), zh_(k+1) = T qh_(k+1) (into qo, zo), pending solution update
-    CU(launch_mr_step<T>(p, qc, qo, zo, wpp, wp, x, st, c->prec_diag, n, L, s), "mr_step");
+    CU(launch_mr_step<T>(p, qc, qo, zo, wpp, wp, x, st, c->prec_diag, c->precf, n, L, s),
+       "mr_step");
     // zh <- Q zh, beta_(k+1)^2 = qh . zh
     TRY(deflate<T>(c, Psi, nv, zo, n, s, qo, st + kMrBnext * n));
     CU(launch_mr_givens(n, st, s), "mr_givens");

@@ -68,9 +68,11 @@ enum { kMrAlpha = 0, kMrBeta, kMrBnext, kMrCpp, kMrSpp, kMrCp, kMrSp, kMrPhibar,
 //   w = (s_(k-1) zh_(k-1) - eps wpp - del wp) ig,  x += t w           -> wpp, x
 // with alpha_k = s_k^2 raw_k (also stored to kMrAlpha), qo holding qh_(k-1)
 // and zo holding zh_(k-1) on entry.  Inactive columns get qh = zh = 0.
+// prec: T = inverse diagonal (FP64), precf its FP32 copy (FP32 blocks).
 template <typename T>
 cudaError_t launch_mr_step(const T *ph, const T *qh, T *qo, T *zo, T *wpp, const T *wp, T *x,
-                           double *st, const double *prec, int n, long long L, cudaStream_t s);
+                           double *st, const double *prec, const float *precf, int n, long long L,
+                           cudaStream_t s);
 // The solution update alone (after the last iteration): w and x as above.
 template <typename T>
 cudaError_t launch_mr_finish(const T *zo, T *wpp, const T *wp, T *x, const double *st, int n,

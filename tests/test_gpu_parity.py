@@ -114,7 +114,7 @@ def test_chebyshev_filter_matches_oracle(cube8):
     assert _colrel(Yg, Y_ora) <= 1e-9
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "tf32"])
 def test_forward_solve_matches_oracle(cube8, prec):
     wl, mesh, d = cube8
     v = d["v_fixed"] + d["v_xc_ref"]
@@ -217,11 +217,11 @@ def test_autograd_backward_is_the_adjoint(cube8):
     assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("prec", ["mixed", "tf32"])
 def test_q4_mixed_solvers_match_oracle(prec):
     """Forward solve and gradient on a Q4 mesh, where the mixed path runs its
-    FP32 cell products on the TF32 tensor cores (prec="mixed") or on the CUDA
-    cores (prec="fp32"); tolerances as above."""
+    FP32 cell products on the CUDA cores (prec="mixed") or, in the Chebyshev
+    filter, on the TF32 tensor cores (prec="tf32"); tolerances as above."""
     mesh = fe.Mesh(-6.0, 6.0, 4, 4)
     xyz = mesh.coords()
     v = W.smeared_coulomb(xyz, np.array([[0.2, -0.3, 0.1]]), np.array([2.0]), 0.5)
@@ -243,3 +243,25 @@ def test_q4_mixed_solvers_match_oracle(prec):
     g = g.cpu().numpy()
     assert abs(loss - L_ora) <= 1e-8 * L_ora
     assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
+
+
+def test_profile_hx_counts_each_kernel_kind():
+    """The per-launch H~X timing of the instrumentation entry point sorts the
+    launches into FP64, FP32 CUDA-core and TF32 tensor-core kinds."""
+    pb = _problem(-6.0, 6.0, 6, 4, nstates=8)
+    L = pb.L
+    pb.set_potential(_cuda(np.zeros(L)))
+    X64 = _cuda(np.random.default_rng(3).standard_normal((L, 12)))
+    X32 = X64.float()
+    pb.profile_hx(True)
+    pb.apply_h(X64)
+    pb.apply_h(X32, tensor_cores=False)
+    pb.apply_h(X32, tensor_cores=True)
+    pb.apply_h(X32, tensor_cores=True)
+    prof = pb.profile_hx(False)
+    assert [prof[k]["launches"] for k in ("fp64", "fp32", "tf32")] == [1, 1, 2]
+    for k in ("fp64", "fp32", "tf32"):
+        assert prof[k]["ms"] > 0 and prof[k]["bytes"] > 0
+    # FP32 on the CUDA cores reads the FP32 copy of v: 4 bytes per node
+    assert prof["fp32"]["bytes"] == (2 * 12 * 4 + 4) * L
+    assert prof["tf32"]["bytes"] == 2 * (2 * 12 * 4 + 8) * L
