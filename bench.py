@@ -48,11 +48,12 @@ import workloads as W  # noqa: E402
 METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 
 # DRAM bytes per (node, column) of one FP32 CUDA-core H~X launch: ncu
-# dram__bytes_read.sum + dram__bytes_write.sum of hx_simt_kernel<64, 0> on the
-# 24^3-cell Q4 mesh (857,375 unknowns) with 60 columns, 415.09 + 158.12 MB,
-# plus the 4-byte zero fill of Z that precedes the kernel in the same launch.
-# Traffic grows with unknowns x columns, so the in-step figure scales by them.
-HX_SIMT_DRAM_BYTES_PER_NODE_COL = (415.09e6 + 158.12e6) / (857375 * 60) + 4.0
+# dram__bytes_read.sum + dram__bytes_write.sum of hx_simt_kernel<64, 0> (TMA
+# brick version) on the 24^3-cell Q4 mesh (857,375 unknowns) with 60 columns,
+# 485.69 + 191.43 MB, plus the 4-byte zero fill of Z that precedes the kernel
+# in the same launch.  Traffic grows with unknowns x columns, so the in-step
+# figure scales by them.
+HX_SIMT_DRAM_BYTES_PER_NODE_COL = (485.69e6 + 191.43e6) / (857375 * 60) + 4.0
 
 # H~X column-applications per inverse iteration on each workload, as counted by
 # the GPU path (line-search solves, Chebyshev passes, MINRES iterations) over the
@@ -70,7 +71,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cube32_q4_e100", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default="cube32_q4_e100",
+                    choices=sorted(W.WORKLOADS) + ["batch16"],
+                    help="batch16: the sixteen small problems stepped as one batch")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-hx", action="store_true", help="skip the operator benchmark")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -391,6 +394,94 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world):
+    """Sixteen small problems (workloads.batch16) stepped as one batch: their
+    Chebyshev filter passes run as single persistent launches while each
+    problem's other work runs on its own stream; timed against the same
+    problems stepped one after another."""
+    import torch
+
+    import paper_2510_10529_b300 as P
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    wls = W.batch16()
+    built = [build_problem(wl, "mixed", device) for wl in wls]
+    rd = [d["rho_data"] for _, d in built]
+    w = [d["w"] for _, d in built]
+
+    def fresh():
+        out = []
+        for wl, (pb0, d) in zip(wls, built):
+            pb = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, wl.nstates,
+                           n_electrons=wl.n_electrons, kT=wl.kT, prec="mixed",
+                           cheb_degree=wl.cheb_degree, seed=wl.seed + 1, device=device)
+            pb.set_potential(d["v_fixed"], None)
+            out.append(pb)
+        return out
+
+    def zeros(pbs):
+        return [torch.zeros(pb.L, dtype=torch.float64, device=device) for pb in pbs]
+
+    # one after another
+    seq = fresh()
+    v_seq = zeros(seq)
+    for _ in range(args.warmup):
+        for b, pb in enumerate(seq):
+            pb.step(rd[b], w[b], v_seq[b])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for b, pb in enumerate(seq):
+            pb.step(rd[b], w[b], v_seq[b])
+    torch.cuda.synchronize()
+    t_seq = (time.perf_counter() - t0) / args.steps
+    for pb in seq:
+        pb.close()
+    # batched
+    probs = fresh()
+    v_b = zeros(probs)
+    batch = P.Batch(probs)
+    for _ in range(args.warmup):
+        batch.step(rd, w, v_b)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = P.invdft_kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(batch.step(rd, w, v_b)[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = P.invdft_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    n = len(wls)
+    line = {
+        "metric": "batched inverse-DFT problem-iterations/s (16 small problems, one batch)",
+        "value": n / (ms / 1e3), "unit": "problem-iter/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "batch16", "problems": n,
+                   "cells": [f"{wl.ncell}^3 Q{wl.order}" for wl in wls],
+                   "n_electrons": [wl.n_electrons for wl in wls],
+                   "nstates": [wl.nstates for wl in wls], "cheb_degree": wls[0].cheb_degree,
+                   "l2": "working sets below L2 size (small problems), no flush",
+                   "parallelism": "one batch"},
+        "sequential": {"value": n / t_seq, "unit": "problem-iter/s",
+                       "ms_per_step": t_seq * 1e3},
+        "batch": batch.info(), "gpu_launches": int(launches), "clocks": clk,
+        "final_err_l2": [s["err_l2"] for s in stats[-1]],
+    }
+    batch.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -423,6 +514,13 @@ def main():
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.workload == "batch16":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the batched workload has no oracle arm; see the default workload"}))
+        elif rank == 0:
+            run_batch(args, rank, world)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

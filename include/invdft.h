@@ -198,6 +198,38 @@ invdft_status invdft_loss_grad(invdft_handle h, const double *rho_data_dev, cons
 invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const double *w_dev,
                           double *v_xc_dev, invdft_stats *stats, void *stream);
 
+/* ---- Batched multi-problem execution.  The paper batches the shifted
+ * adjoint systems of one problem into one block solve (Sec. 3.2.2); this
+ * batches whole independent problems (no further counterpart in the paper).
+ * invdft_batch_create: handles bound, in INVDFT_MIXED or INVDFT_MIXED_TF32
+ * precision, with equal Chebyshev degree in [2, 64] and nstates <= 256;
+ * n in [1, 64], no handle twice.  The batch keeps the handle pointers: they
+ * must outlive it, and no other call may use them while a batch step runs.
+ * EINVAL on bad arguments, ECUDA if its streams or device tables cannot be
+ * created.
+ * invdft_batch_step: one invdft_step of every problem.  rho_data, w, v_xc
+ * are host arrays of n device pointers (v_xc[b] in/out, [L_b] each); stats
+ * and status (optional) are host arrays of n receiving each problem's
+ * statistics and status.  The problems run concurrently, each on its own
+ * stream; each pass of their Chebyshev filters (the defect-corrected FP32
+ * recurrence) is combined with the passes of the other problems waiting at
+ * that moment into one cooperative persistent kernel over a device work
+ * queue of (phase, problem, cell tile) items, launched from a captured CUDA
+ * graph per set of problems.  The first call autotunes the column chunk of
+ * each (order, width) class.  Ordered after `stream`; `stream` waits for the
+ * whole step; returns the worst status (ETIMEOUT if a phase wait of the
+ * persistent kernel gave up).
+ * invdft_batch_info: chunk_cols[b] (host, n; optional) = the column chunk of
+ * problem b; info4 (optional) = {batched filter launches, of which CUDA-graph
+ * replays, persistent CTAs per launch, autotuned (0/1)}.                    */
+typedef struct invdft_batch_ctx *invdft_batch;
+invdft_status invdft_batch_create(const invdft_handle *handles, int n, invdft_batch *out);
+invdft_status invdft_batch_destroy(invdft_batch batch);
+invdft_status invdft_batch_step(invdft_batch batch, const double *const *rho_data_dev,
+                                const double *const *w_dev, double *const *v_xc_dev,
+                                invdft_stats *stats, invdft_status *status, void *stream);
+invdft_status invdft_batch_info(invdft_batch batch, int *chunk_cols, double *info4);
+
 /* Instrumentation for benchmarks (no counterpart in the paper).
  * invdft_profile_hx: while enabled, every H~X launch of this handle is
  * bracketed by CUDA events on its stream.  Each call first drains pending

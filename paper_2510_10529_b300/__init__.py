@@ -17,7 +17,7 @@ import torch
 from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_MIXED, INVDFT_MIXED_TF32, INVDFT_OK,
                    InvdftError, MeshDesc, Opts, Stats, check, lib)
 
-__all__ = ["Problem", "KohnShamDensity", "MeshDesc", "Opts", "Stats", "InvdftError",
+__all__ = ["Problem", "Batch", "KohnShamDensity", "MeshDesc", "Opts", "Stats", "InvdftError",
            "INVDFT_FP64", "INVDFT_MIXED", "INVDFT_MIXED_TF32", "library_path"]
 
 
@@ -265,6 +265,65 @@ class Problem:
 
     def profile_hx(self, enable: bool):
         return invdft_profile_hx(self.h, enable)
+
+
+def invdft_batch_create(handles) -> int:
+    arr = (C.c_void_p * len(handles))(*handles)
+    out = C.c_void_p()
+    _ok("invdft_batch_create", lib.invdft_batch_create(arr, len(handles), C.byref(out)), None,
+        False)
+    return out.value
+
+
+def invdft_batch_step(batch, handles, rho_data, w, v_xc):
+    n = len(handles)
+    ptrs = [(C.c_void_p * n)(*[_ptr(t) for t in ts]) for ts in (rho_data, w, v_xc)]
+    stats = (Stats * n)()
+    status = (C.c_int * n)()
+    code = lib.invdft_batch_step(batch, ptrs[0], ptrs[1], ptrs[2], stats, status, _stream())
+    if code not in (INVDFT_OK, INVDFT_ENOCONV):
+        text = "; ".join(f"problem {b}: status {status[b]}: "
+                         + lib.invdft_last_error(handles[b]).decode(errors="replace")
+                         for b in range(n) if status[b] not in (INVDFT_OK, INVDFT_ENOCONV))
+        raise InvdftError("invdft_batch_step", code, text)
+    return [stats[b].as_dict() for b in range(n)], [int(status[b]) for b in range(n)]
+
+
+class Batch:
+    """Independent problems stepped together (invdft_batch_*): each problem's
+    step runs on its own stream and the Chebyshev filter passes of all of
+    them run as single cooperative persistent launches."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.h = invdft_batch_create([p.h for p in self.problems])
+
+    def step(self, rho_data, w, v_xc):
+        stats, status = invdft_batch_step(self.h, [p.h for p in self.problems], rho_data, w,
+                                          v_xc)
+        for p in self.problems:
+            p.potential_version += 1
+            p.solved_version = p.potential_version
+        return stats, status
+
+    def info(self):
+        n = len(self.problems)
+        cols = (C.c_int * n)()
+        info = (C.c_double * 4)()
+        _ok("invdft_batch_info", lib.invdft_batch_info(self.h, cols, info), None, False)
+        return {"chunk_cols": list(cols), "launches": int(info[0]),
+                "graph_launches": int(info[1]), "ctas": int(info[2]), "tuned": bool(info[3])}
+
+    def close(self):
+        if self.h:
+            lib.invdft_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class KohnShamDensity(torch.autograd.Function):

@@ -81,6 +81,10 @@ def _load():
         "invdft_profile_hx": [H, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
         "invdft_loss_reduce_noalloc": [P, P, P, P, C.c_longlong, P, P, P],
+        "invdft_batch_create": [P, C.c_int, C.POINTER(H)],
+        "invdft_batch_destroy": [H],
+        "invdft_batch_step": [H, P, P, P, C.POINTER(Stats), P, P],
+        "invdft_batch_info": [H, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -6,6 +6,8 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "internal.h"
@@ -14,6 +16,20 @@
 using namespace invdft;
 
 namespace invdft {
+
+cudaError_t raise_smem_limit(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &cur = limit[{dev, func}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
 
 static thread_local std::string g_create_error;
 static std::atomic<unsigned long long> g_launches{0};

@@ -277,8 +277,7 @@ cudaError_t launch_rotate(const double *Xi, int n1, const double *Cm, int n2, lo
   if (n1 < 1 || n2 < 1 || n1 > kMaxGram || n2 > kMaxGram) return cudaErrorInvalidValue;
   const int rpp = std::max(1, 256 / n2);
   const size_t smem = sizeof(double) * ((size_t)n1 * n2 + (size_t)rpp * n1);
-  cudaError_t e = cudaFuncSetAttribute(rotate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit(rotate_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   rotate_kernel<<<148 * 4, 256, smem, s>>>(Xi, n1, Cm, n2, L, Xo);
@@ -294,8 +293,7 @@ cudaError_t launch_rotate_acc(const T *Xi, int n1, const double *Cm, int n2, lon
   if (n1 < 1 || n2 < 1 || n1 > kMaxGram || n2 > kMaxGram) return cudaErrorInvalidValue;
   const int rpp = std::max(1, 256 / n2);
   const size_t smem = sizeof(T) * ((size_t)n1 * n2 + (size_t)rpp * n1);
-  cudaError_t e = cudaFuncSetAttribute(rotate_acc_kernel<T>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(rotate_acc_kernel<T>, (int)smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   rotate_acc_kernel<T><<<148 * 4, 256, smem, s>>>(Xi, n1, Cm, n2, L, Xo, alpha);
@@ -494,8 +492,7 @@ cudaError_t launch_stripe_gram(const T *A, int n1, const T *B, int n2, long long
   const size_t stage = 2 * (size_t)kSgRows * (n1 + n2) * sizeof(T);
   const size_t red = (size_t)S * tiles * 16 * sizeof(TA);
   const size_t smem = std::max(stage, red);
-  cudaError_t e = cudaFuncSetAttribute(stripe_gram<T, TA>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(stripe_gram<T, TA>, smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   stripe_gram<T, TA><<<kGramBlocks, 256, smem, s>>>(A, n1, B, n2, L, partial);
@@ -513,8 +510,7 @@ cudaError_t launch_stripe_rotate(const T *Psi, int n1, const double *C, int n2, 
     const int ncg = (n2 + NJ - 1) / NJ;
     const int rows_blk = 256 / ncg;
     const size_t smem = sizeof(T) * ((size_t)n1 * ncg * NJ + (size_t)rows_blk * (n1 + 1));
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = raise_smem_limit(kern, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<long long>((L + rows_blk - 1) / rows_blk, 148LL * 8);
     ::invdft::count_launch();
@@ -701,7 +697,7 @@ cudaError_t launch_gram_rr(const double *Y, const double *HY, int n, long long L
   // staging ring, and room for the stripe sums (at most 256 x 16 doubles)
   const size_t smem = std::max(4 * (size_t)kRrRows * n, (size_t)256 * 16) * sizeof(double);
   cudaError_t e =
-      cudaFuncSetAttribute(gram_rr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      raise_smem_limit(gram_rr_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   gram_rr_kernel<<<kGramBlocks, 256, smem, s>>>(Y, HY, n, L, partial);

@@ -333,8 +333,7 @@ cudaError_t launch_defl_gram_f32(const float *Psi, int n1p, const float *Z, int 
   const int nblk = kGramBlocks;
   const size_t smem =
       std::max((size_t)kDgStages * kDgRows * (n1p + n2p), (size_t)256 * 32) * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(defl_gram_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(defl_gram_kernel, (int)smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   defl_gram_kernel<<<nblk, 256, smem, s>>>(Psi, n1p, Z, n2p, L, partial);
@@ -354,8 +353,7 @@ cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, i
   const int grid = (int)std::min<long long>(ntile, (long long)num_sms() * 2);
   cudaError_t e;
   if (V) {
-    e = cudaFuncSetAttribute(defl_update_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem_limit(defl_update_kernel<true>, (int)smem);
     if (e != cudaSuccess) return e;
     ::invdft::count_launch();
     defl_update_kernel<true><<<grid, 256, smem, s>>>(Psi, n1p, ldp, C, n2p, L, Z, alpha, V,
@@ -363,8 +361,7 @@ cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, i
     ::invdft::count_launch();
     defl_sum_partials<<<(n2p + 31) / 32, 256, 0, s>>>(partial, grid, n2p, dot_out);
   } else {
-    e = cudaFuncSetAttribute(defl_update_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem_limit(defl_update_kernel<false>, (int)smem);
     if (e != cudaSuccess) return e;
     ::invdft::count_launch();
     defl_update_kernel<false><<<grid, 256, smem, s>>>(Psi, n1p, ldp, C, n2p, L, Z, alpha,

@@ -252,8 +252,7 @@ cudaError_t launch_rr_small(const double *S, const double *H, int n, double *the
                             int *status, double *work, cudaStream_t s) {
   if (n < 1 || n > kMaxDense) return cudaErrorInvalidValue;
   const size_t smem = 2 * (size_t)n * n * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(rr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = raise_smem_limit(rr_small, (int)smem);
   if (e != cudaSuccess) return e;
   ::invdft::count_launch();
   rr_small<<<1, 1024, smem, s>>>(S, H, n, theta, C, status, work, work + (size_t)n * n, 60);

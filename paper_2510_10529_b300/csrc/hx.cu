@@ -239,7 +239,7 @@ cudaError_t run_cells(const Geom &g, const T *X, T *Z, int ncol, double scale, c
   constexpr int Q = P + 1, NE = Q * Q * Q;
   const size_t smem = 2 * (size_t)NE * C * sizeof(T);
   auto k = hx_cells<T, P, C>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(k, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(g.ncell * g.ncell * g.ncell, (ncol + C - 1) / C);
   ::invdft::count_launch();

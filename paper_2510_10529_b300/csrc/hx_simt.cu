@@ -319,7 +319,7 @@ template <int C, bool HW>
 cudaError_t run_simt(const SmArgs &p, const CUtensorMap &tm, long long items, cudaStream_t s) {
   const size_t smem = 3 * (size_t)kNe * C * sizeof(float) + 128;
   auto k = hx_simt_kernel<C, HW>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_smem_limit(k, (int)smem);
   if (e != cudaSuccess) return e;
   int nsm = 148, per_sm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);

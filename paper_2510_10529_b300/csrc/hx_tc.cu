@@ -431,7 +431,7 @@ cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a,
       {hx_tc_kernel<64, false, false>, hx_tc_kernel<64, true, false>,
        hx_tc_kernel<64, false, true>, hx_tc_kernel<64, true, true>}};
   const K kern = table[C == 16 ? 0 : (C == 32 ? 1 : 2)][mode];
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = raise_smem_limit(kern, (int)smem);
   if (e != cudaSuccess) return e;
   TcArgs p;
   p.X = a.X;

@@ -69,8 +69,22 @@ struct HxProf {
   long long n[3] = {0, 0, 0};
 };
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) that only ever raises a
+// kernel's limit (api.cu).  Several host threads may launch the same kernel
+// with different shared-memory sizes (problems of a batch); a smaller limit
+// set by one thread must never undercut a launch of another.
+cudaError_t raise_smem_limit(const void *func, size_t bytes);
+template <typename F>
+cudaError_t raise_smem_limit(F *func, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void *>(func), bytes);
+}
+
+struct BatchState;                  // batch_api.cu
+
 struct Ctx {
   HxProf prof;
+  BatchState *batch = nullptr;      // set while a batch step runs this problem
+  int batch_index = -1;
   invdft_mesh_desc mesh{};
   invdft_opts o{};
   Tables tab;

@@ -13,20 +13,13 @@
 
 #include "internal.h"
 #include "solvers.h"
+#include "batch.h"
 
 namespace invdft {
 
 namespace {
 
 // Offsets (in doubles) inside the per-handle scalar area c->scal.
-constexpr size_t kScMisc = 0;                       // dots, loss sums
-constexpr size_t kScMu = 32;                        // chemical potential
-constexpr size_t kScRes = 64;                       // Ritz residual norms^2 [nv]
-constexpr size_t kScCol = 512;                      // column dots [<= 256]
-constexpr size_t kScAdj = 200 * (size_t)kMaxCols;   // adjoint per-column tables
-constexpr size_t kScMr = 256 * (size_t)kMaxCols;    // MINRES scalars
-constexpr size_t kScInt = 400 * (size_t)kMaxCols;   // adjoint int tables
-constexpr size_t kScPk = 512 * (size_t)kMaxCols;    // Chebyshev p_k(theta) table
 
 inline void set_tc(HxArgs<double> &, bool) {}
 inline void set_tc(HxArgs<float> &a, bool on) { a.tc = on; }
@@ -270,7 +263,22 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
   float *D1 = (float *)c->C0;
   CU(launch_scale_f32(E, nullptr, sigma1 / e, ncol, L, D1, s), "scale(D1)");
   const void *prev = nullptr, *cur = D1;
-  for (int k = 2; k <= m; ++k) {
+  const bool batched = c->batch && m >= 2 && m <= kMaxBatchDeg;
+  if (batched) {
+    // batched step: phases 2..m of every waiting problem in one launch;
+    // D_2, D_3 accumulate into zeroed buffers, later outputs are zeroed by
+    // the owners of their nodes
+    std::vector<double> al(m + 1, 0.0), be(m + 1, 0.0);
+    for (int k = 2; k <= m; ++k) {
+      al[k] = 2.0 * sig[k] / e;
+      be[k] = k >= 3 ? -sig[k - 1] * sig[k] : 0.0;
+    }
+    CU(cudaMemsetAsync(bufs[1], 0, (size_t)L * ncol * sizeof(float), s), "memset");
+    CU(cudaMemsetAsync(bufs[2], 0, (size_t)L * ncol * sizeof(float), s), "memset");
+    TRY(batch_filter_submit(c, m, al.data(), be.data(), cc, s));
+    cur = bufs[(m - 1) % 3];
+  }
+  for (int k = 2; k <= m && !batched; ++k) {
     const double sn = sig[k];
     void *Z = free_buf(prev, cur);
     HxArgs<float> h;

@@ -5,6 +5,16 @@
 
 namespace invdft {
 
+// Layout of the per-handle scalar area c->scal (doubles)
+constexpr size_t kScMisc = 0;                       // dots, loss sums
+constexpr size_t kScMu = 32;                        // chemical potential
+constexpr size_t kScRes = 64;                       // Ritz residual norms^2 [nv]
+constexpr size_t kScCol = 512;                      // column dots [<= 256]
+constexpr size_t kScAdj = 200 * (size_t)kMaxCols;   // adjoint per-column tables
+constexpr size_t kScMr = 256 * (size_t)kMaxCols;    // MINRES scalars
+constexpr size_t kScInt = 400 * (size_t)kMaxCols;   // adjoint int tables
+constexpr size_t kScPk = 512 * (size_t)kMaxCols;    // Chebyshev p_k(theta) table
+
 // ---- dense.cu
 cudaError_t launch_rr_small(const double *S, const double *H, int n, double *theta, double *C,
                             int *status, double *work, cudaStream_t s);

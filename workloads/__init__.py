@@ -116,6 +116,30 @@ def cube32_q4_e100() -> Workload:
                     nuclei_R=R, nuclei_Z=Z, cheb_degree=30, seed=4000)
 
 
+def batch16() -> list:
+    """Sixteen independent small problems for batched execution: cells per axis
+    uniform in 8..16, order 2 or 4, electrons from {2, 4, 6, 10, 14, 20}, one
+    to three nuclei (charges rescaled to the electron count) in the inner half
+    of a [-8, 8]^3 box, one Gaussian bump each, nstates = N_e/2 + ceil(N_e/10)
+    + 2, a common Chebyshev degree 20, kT = 500 K."""
+    out = []
+    for i in range(16):
+        rng = _rng(5, i)
+        ncell = int(rng.integers(8, 17))
+        order = int(rng.choice([2, 4]))
+        ne = float(rng.choice([2, 4, 6, 10, 14, 20]))
+        nn = int(rng.integers(1, 4))
+        Z = _neutral_charges(rng, nn, ne)
+        R = rng.uniform(-4.0, 4.0, size=(nn, 3))
+        centre = R[int(rng.integers(0, nn))] + rng.uniform(-1.0, 1.0, size=3)
+        out.append(Workload(name=f"batch16_{i}", lo=-8.0, hi=8.0, ncell=ncell, order=order,
+                            n_electrons=ne, nstates=int(ne // 2 + math.ceil(ne / 10) + 2),
+                            kT=KT_DEFAULT, nuclei_R=R, nuclei_Z=Z,
+                            bump_c=centre[None, :], bump_a=np.array([0.1]),
+                            bump_b=np.array([1.0]), cheb_degree=20, seed=5000 + i))
+    return out
+
+
 def tiny(ncell=3, order=2, half=4.0, n_electrons=2.0, nstates=4, kT=0.0,
          Z=(2.0,), R=((0.0, 0.0, 0.0),), seed=9000) -> Workload:
     """Tiny meshes for brute-force checks (dense eigensolves, finite differences)."""
