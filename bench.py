@@ -475,7 +475,8 @@ def run_batch(args, rank, world):
                    "parallelism": "one batch"},
         "sequential": {"value": n / t_seq, "unit": "problem-iter/s",
                        "ms_per_step": t_seq * 1e3},
-        "batch": batch.info(), "gpu_launches": int(launches), "clocks": clk,
+        "batch": batch.info(), "graphs": P.invdft_graph_stats(), "gpu_launches": int(launches),
+        "clocks": clk,
         "final_err_l2": [s["err_l2"] for s in stats[-1]],
     }
     batch.close()

@@ -241,9 +241,12 @@ invdft_status invdft_batch_info(invdft_batch batch, int *chunk_cols, double *inf
  * tensor-core kernel.
  * enable = 1 resets the totals and turns timing on; 0 turns it off.
  * invdft_kernel_launches: process-wide count of kernels launched by this
- * library since it was loaded.                                              */
+ * library since it was loaded (kernels run by CUDA-graph replays included).
+ * invdft_graph_stats: out3 = {graphs captured, graph replays, captures the
+ * runtime refused (the work then ran as plain launches)}, process-wide.     */
 invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12);
 invdft_status invdft_kernel_launches(unsigned long long *count);
+invdft_status invdft_graph_stats(long long *out3);
 
 /* Allocation-free loss reduction.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory -- a host

@@ -153,6 +153,12 @@ def invdft_profile_hx(h, enable: bool):
             "tf32": dict(zip(keys, out[8:]))}
 
 
+def invdft_graph_stats() -> dict:
+    out = (C.c_longlong * 3)()
+    lib.invdft_graph_stats(out)
+    return {"captured": int(out[0]), "replays": int(out[1]), "refused": int(out[2])}
+
+
 def invdft_kernel_launches() -> int:
     n = C.c_ulonglong()
     lib.invdft_kernel_launches(C.byref(n))

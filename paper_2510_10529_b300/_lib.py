@@ -80,6 +80,7 @@ def _load():
         "invdft_reset": [H],
         "invdft_profile_hx": [H, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
+        "invdft_graph_stats": [P],
         "invdft_loss_reduce_noalloc": [P, P, P, P, C.c_longlong, P, P, P],
         "invdft_batch_create": [P, C.c_int, C.POINTER(H)],
         "invdft_batch_destroy": [H],

@@ -2,6 +2,7 @@
 // life cycle, workspace binding, tables, potential, and the operator calls.
 // The solver entry points (forward, adjoint, loss/gradient, step) live in
 // solvers.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,15 +27,38 @@ cudaError_t raise_smem_limit(const void *func, size_t bytes) {
   std::lock_guard<std::mutex> lk(mu);
   size_t &cur = limit[{dev, func}];
   if (bytes <= cur) return cudaSuccess;
-  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) cur = bytes;
+  // the first time, raise the limit to the device's opt-in maximum, so that
+  // it never has to change later (a change while a stream is being captured
+  // into a CUDA graph would invalidate the capture)
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  size_t target = std::max(bytes, (size_t)optin);
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)target);
+  if (e != cudaSuccess && target != bytes) {
+    cudaGetLastError();
+    target = bytes;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)target);
+  }
+  if (e == cudaSuccess) cur = target;
   return e;
 }
 
 static thread_local std::string g_create_error;
 static std::atomic<unsigned long long> g_launches{0};
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local unsigned long long t_launches = 0;   // launches issued by this thread
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void count_launches(long long n) {
+  g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+  t_launches += (unsigned long long)n;
+}
+unsigned long long thread_launches() { return t_launches; }
+static std::atomic<long long> g_graph_stats[3];            // captures, replays, refused captures
+void count_graph(int what) { g_graph_stats[what].fetch_add(1, std::memory_order_relaxed); }
 void set_global_error(const char *msg) { g_create_error = msg; }
 
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what) {
@@ -392,6 +416,12 @@ invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12) {
     }
   }
   p.on = enable != 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_graph_stats(long long *out3) {
+  if (!out3) return INVDFT_EINVAL;
+  for (int k = 0; k < 3; ++k) out3[k] = g_graph_stats[k].load(std::memory_order_relaxed);
   return INVDFT_OK;
 }
 

@@ -32,6 +32,9 @@ cudaError_t launch_batch_filter(const BatchProb *d_probs, int nprob, int m, int 
 // buffers, tables); C, item counts and the per-pass scalars are set later.
 void batch_prob_static(const Ctx *c, BatchProb *bp);
 
+// Chebyshev degree of the batch a problem belongs to (0 if none).
+int batch_degree(const Ctx *c);
+
 // Hands the defect-corrected filter of a problem taking part in a batch step
 // to the batch (D_1 formed, outputs zeroed and p_k pushed on stream s), and
 // returns once the batched launch is queued; s then waits for it.

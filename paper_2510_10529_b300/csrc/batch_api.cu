@@ -12,6 +12,7 @@
 // chunk of each problem's items is chosen per (order, width) class by a small
 // autotuner on the first step.
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <map>
@@ -62,6 +63,10 @@ struct BatchState {
 };
 
 namespace {
+
+// How long a posted filter waits for the other problems of the batch
+constexpr long long kFilterWindowUs = 500;
+constexpr size_t kMaxGraphs = 64;   // cached launch graphs (sets of problems)
 
 int chunk_candidates(int ncol, int out[3]) {
   int n = 0;
@@ -133,7 +138,7 @@ invdft_status launch_locked(BatchState *B) {
   bool done = false;
   if (B->graphs_ok) {
     auto it = B->graphs.find(mask);
-    if (it == B->graphs.end()) {
+    if (it == B->graphs.end() && B->graphs.size() < kMaxGraphs) {
       // capture the sequence once for this set of problems
       cudaGraph_t g = nullptr;
       cudaGraphExec_t ge = nullptr;
@@ -143,8 +148,10 @@ invdft_status launch_locked(BatchState *B) {
         if (ce == cudaSuccess && ee == cudaSuccess &&
             cudaGraphInstantiate(&ge, g, 0) == cudaSuccess) {
           it = B->graphs.emplace(mask, ge).first;
+          count_graph(0);
         } else {
           B->graphs_ok = false;
+          count_graph(2);
         }
         if (g) cudaGraphDestroy(g);
       } else {
@@ -155,6 +162,7 @@ invdft_status launch_locked(BatchState *B) {
     if (B->graphs_ok && it != B->graphs.end()) {
       e = cudaGraphLaunch(it->second, B->bstream);
       ++B->graph_launches;
+      count_graph(1);
       done = true;
     }
   }
@@ -266,6 +274,8 @@ void batch_prob_static(const Ctx *c, BatchProb *bp) {
   eo_tables(c->g, bp->tab);
 }
 
+int batch_degree(const Ctx *c) { return c->batch ? c->batch->degree : 0; }
+
 invdft_status batch_filter_submit(Ctx *c, int m, const double *alpha, const double *beta,
                                   double shift, cudaStream_t s) {
   BatchState *B = c->batch;
@@ -293,8 +303,11 @@ invdft_status batch_filter_submit(Ctx *c, int m, const double *alpha, const doub
     const unsigned long long my = B->gen;
     if (B->arrived == B->active) {
       release_locked(B, launch_locked(B));
-    } else {
-      B->cv.wait(lk, [&] { return B->gen != my; });
+    } else if (!B->cv.wait_for(lk, std::chrono::microseconds(kFilterWindowUs),
+                               [&] { return B->gen != my; })) {
+      // the other problems are busy elsewhere (Rayleigh-Ritz, adjoint):
+      // launch for those that have posted; the rest join a later launch
+      release_locked(B, launch_locked(B));
     }
     st = B->last_launch;
     if (st != INVDFT_OK) c->err = B->err;

@@ -271,8 +271,11 @@ defl_update_kernel(const float *__restrict__ Psi, int n1p, int ldp, const double
 }
 
 int num_sms() {
-  int nsm = 148;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
+  static const int nsm = [] {
+    int n = 148;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, 0);
+    return n;
+  }();
   return nsm;
 }
 

@@ -321,11 +321,17 @@ cudaError_t run_simt(const SmArgs &p, const CUtensorMap &tm, long long items, cu
   auto k = hx_simt_kernel<C, HW>;
   cudaError_t e = raise_smem_limit(k, (int)smem);
   if (e != cudaSuccess) return e;
-  int nsm = 148, per_sm = 1;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, simt_threads<C>(), smem);
-  if (e != cudaSuccess) return e;
-  const int grid = (int)std::min<long long>(items, (long long)nsm * std::max(per_sm, 1));
+  // resident CTAs per SM: queried once per kernel variant (no device queries
+  // while a stream may be capturing a graph)
+  static const int resident = [&] {
+    int nsm = 148, per_sm = 1;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, simt_threads<C>(), smem) !=
+        cudaSuccess)
+      per_sm = 1;
+    return nsm * std::max(per_sm, 1);
+  }();
+  const int grid = (int)std::min<long long>(items, (long long)resident);
   ::invdft::count_launch();
   k<<<grid, simt_threads<C>(), smem, s>>>(p, tm);
   return cudaGetLastError();

@@ -150,6 +150,12 @@ namespace invdft {
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what);
 // process-wide count of kernels this library has launched (benchmark evidence)
 void count_launch();
+// n kernels run by a graph replay (negative: take back launches counted while
+// capturing a graph); launches counted so far by this thread
+void count_launches(long long n);
+unsigned long long thread_launches();
+// process-wide CUDA-graph counters: 0 captures, 1 replays, 2 refused captures
+void count_graph(int what);
 #define INV_CUDA(c, call)                                   \
   do {                                                      \
     if (!::invdft::cuda_ok((c), (call), #call)) return INVDFT_ECUDA; \

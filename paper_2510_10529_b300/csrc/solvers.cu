@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "internal.h"
@@ -39,6 +40,32 @@ invdft_status fetch(Ctx *c, const void *dev, size_t bytes, void *host, cudaStrea
   INV_CUDA(c, cudaMemcpyAsync(c->hbuf, dev, bytes, cudaMemcpyDeviceToHost, s));
   INV_CUDA(c, cudaStreamSynchronize(s));
   std::memcpy(host, c->hbuf, bytes);
+  return INVDFT_OK;
+}
+
+// Several small device reads with one synchronisation: the pieces are staged
+// one after another in the pinned buffer (16 kMaxCols doubles in all).
+struct Piece {
+  const void *dev;
+  size_t bytes;
+  void *host;
+};
+invdft_status fetch_many(Ctx *c, std::initializer_list<Piece> pieces, cudaStream_t s) {
+  size_t off = 0;
+  for (const Piece &p : pieces) {
+    if (off + p.bytes > 16 * kMaxCols * sizeof(double)) {
+      c->err = "fetch_many: pieces exceed the staging buffer";
+      return INVDFT_EINVAL;
+    }
+    INV_CUDA(c, cudaMemcpyAsync((char *)c->hbuf + off, p.dev, p.bytes, cudaMemcpyDeviceToHost, s));
+    off += (p.bytes + 7) & ~(size_t)7;
+  }
+  INV_CUDA(c, cudaStreamSynchronize(s));
+  off = 0;
+  for (const Piece &p : pieces) {
+    std::memcpy(p.host, (const char *)c->hbuf + off, p.bytes);
+    off += (p.bytes + 7) & ~(size_t)7;
+  }
   return INVDFT_OK;
 }
 
@@ -263,7 +290,9 @@ invdft_status run_filter(Ctx *c, const void *X, void *Y, int ncol, int m, double
   float *D1 = (float *)c->C0;
   CU(launch_scale_f32(E, nullptr, sigma1 / e, ncol, L, D1, s), "scale(D1)");
   const void *prev = nullptr, *cur = D1;
-  const bool batched = c->batch && m >= 2 && m <= kMaxBatchDeg;
+  // inside a batch step the passes of the batch's degree are batched; a pass
+  // of another degree (a repeated pass) runs on its own
+  const bool batched = c->batch && m >= 2 && m <= kMaxBatchDeg && batch_degree(c) == m;
   if (batched) {
     // batched step: phases 2..m of every waiting problem in one launch;
     // D_2, D_3 accumulate into zeroed buffers, later outputs are zeroed by
@@ -335,11 +364,11 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
   for (;;) {
     CU(launch_occupations(c->eps, n, c->o.n_electrons, c->o.kT, c->occ, c->dfde, c->scal + kScMu,
                           c->status, s), "occupations");
-    TRY(fetch(c, c->eps, n * sizeof(double), theta.data(), s));
-    TRY(fetch(c, c->occ, n * sizeof(double), occ.data(), s));
-    TRY(fetch(c, c->scal + kScRes, n * sizeof(double), res2.data(), s));
     int occ_status = 0;
-    TRY(fetch(c, c->status + 1, sizeof(int), &occ_status, s));
+    TRY(fetch_many(c, {{c->eps, n * sizeof(double), theta.data()},
+                       {c->occ, n * sizeof(double), occ.data()},
+                       {c->scal + kScRes, n * sizeof(double), res2.data()},
+                       {c->status + 1, sizeof(int), &occ_status}}, s));
     if (occ_status) {
       c->err = "occupations: kT = 0 needs an even electron count and nstates > N_e/2";
       return INVDFT_EINVAL;
@@ -356,16 +385,23 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
     const double a = theta[n - 1], a0 = theta[0];
     double b = c->upper_bound;
     if (!(b > a)) b = a + std::max(1.0, std::fabs(a));
-    if (c->o.prec == INVDFT_FP64) {
-      TRY(run_filter(c, c->X, c->Y, n, c->o.cheb_degree, a, b, a0, INVDFT_FP64, nullptr, nullptr, s));
-    } else {
-      TRY(run_filter(c, c->X, c->Y, n, c->o.cheb_degree, a, b, a0, INVDFT_MIXED, theta.data(),
-                     c->E32, s));
+    // a pass whose filtered block is numerically rank deficient (the filter
+    // damps the top of a very wide wanted interval below FP64 resolution) is
+    // repeated from the same Ritz vectors with half the degree; Rayleigh-Ritz
+    // fails before it overwrites them
+    for (int m = c->o.cheb_degree;; m = std::max(1, m / 2)) {
+      if (c->o.prec == INVDFT_FP64) {
+        TRY(run_filter(c, c->X, c->Y, n, m, a, b, a0, INVDFT_FP64, nullptr, nullptr, s));
+      } else {
+        TRY(run_filter(c, c->X, c->Y, n, m, a, b, a0, INVDFT_MIXED, theta.data(), c->E32, s));
+      }
+      hx_calls += m;
+      TRY(apply_h_f64(c, c->Y, c->HY, n, s));
+      ++hx_calls;
+      const invdft_status rr = rayleigh_ritz(c, s);
+      if (rr == INVDFT_OK) break;
+      if (rr != INVDFT_ENOTSPD || m == 1) return rr;
     }
-    hx_calls += c->o.cheb_degree;
-    TRY(apply_h_f64(c, c->Y, c->HY, n, s));
-    ++hx_calls;
-    TRY(rayleigh_ritz(c, s));
     ++pass;
   }
   CU(launch_density(c->X, n, c->occ, c->mass, L, c->rho, s), "density");
@@ -473,15 +509,8 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int n
   CU(cudaMemsetAsync(wpp, 0, blk * sizeof(T), s), "memset");
   CU(cudaMemsetAsync(wp, 0, blk * sizeof(T), s), "memset");
   CU(cudaMemsetAsync(x, 0, blk * sizeof(T), s), "memset");
-  int it = 0;
-  std::vector<double> act(n);
-  for (; it < maxit; ++it) {
-    if (it % 4 == 0) {
-      TRY(fetch(c, st + kMrActive * n, n * sizeof(double), act.data(), s));
-      bool any = false;
-      for (int j = 0; j < n; ++j) any |= act[j] != 0.0;
-      if (!any) break;
-    }
+  // one MINRES iteration on the current buffer roles (no host synchronisation)
+  auto iteration = [&]() -> invdft_status {
     HxArgs<T> a;
     // the inner MINRES operator stays on the FP32 CUDA cores: with TF32
     // operands (relative error ~3e-4) the inner solves stall early and the
@@ -503,7 +532,66 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int n
     std::swap(qc, qo);
     std::swap(zc, zo);
     std::swap(wpp, wp);
+    return INVDFT_OK;
+  };
+  // Iterations run in groups of kMrGroup between convergence checks.  Past
+  // the first group, a group (two periods of the buffer rotation, so the
+  // roles repeat) is captured once as a CUDA graph and replayed: small
+  // problems are otherwise bound by launch latency.  Not while H~X launches
+  // are being timed (their events would be captured too).
+  constexpr int kMrGroup = 4;
+  cudaGraphExec_t group = nullptr;
+  long long group_kernels = 0;
+  bool graphs = !c->prof.on;
+  int it = 0;
+  std::vector<double> act(n);
+  invdft_status result = INVDFT_OK;
+  while (it < maxit && result == INVDFT_OK) {
+    result = fetch(c, st + kMrActive * n, n * sizeof(double), act.data(), s);
+    if (result != INVDFT_OK) break;
+    bool any = false;
+    for (int j = 0; j < n; ++j) any |= act[j] != 0.0;
+    if (!any) break;
+    if (graphs && it >= kMrGroup && it + kMrGroup <= maxit) {
+      if (!group) {
+        T *roles[6] = {qc, qo, zc, zo, wpp, wp};
+        const unsigned long long k0 = thread_launches();
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          invdft_status cst = INVDFT_OK;
+          for (int j = 0; j < kMrGroup && cst == INVDFT_OK; ++j) cst = iteration();
+          ok = cudaStreamEndCapture(s, &g) == cudaSuccess && cst == INVDFT_OK;
+        }
+        if (ok) ok = cudaGraphInstantiate(&group, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        // nothing captured has run: restore the roles and the launch count
+        qc = roles[0], qo = roles[1], zc = roles[2], zo = roles[3], wpp = roles[4], wp = roles[5];
+        group_kernels = (long long)(thread_launches() - k0);
+        count_launches(-group_kernels);
+        count_graph(ok ? 0 : 2);
+        if (!ok) {
+          group = nullptr;
+          graphs = false;
+          continue;
+        }
+      }
+      if (cudaGraphLaunch(group, s) != cudaSuccess) {
+        c->err = "minres: graph launch failed";
+        result = INVDFT_ECUDA;
+        break;
+      }
+      count_launches(group_kernels);
+      count_graph(1);
+      it += kMrGroup;
+      continue;
+    }
+    for (int j = 0; j < kMrGroup && it < maxit && result == INVDFT_OK; ++j, ++it)
+      result = iteration();
   }
+  if (group) cudaGraphExecDestroy(group);
+  if (result != INVDFT_OK) return result;
   CU(launch_mr_finish<T>(zo, wpp, wp, x, st, n, L, s), "mr_finish");
   std::vector<double> itv(n);
   TRY(fetch(c, st + kMrIters * n, n * sizeof(double), itv.data(), s));
