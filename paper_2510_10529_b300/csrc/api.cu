@@ -225,6 +225,11 @@ invdft_status invdft_destroy(invdft_handle h) {
   if (!h) return INVDFT_EINVAL;
   if (h->hbuf) cudaFreeHost(h->hbuf);
   for (auto e : h->prof.ev) cudaEventDestroy(e);
+  if (h->aux_stream) {
+    cudaStreamSynchronize(h->aux_stream);
+    cudaStreamDestroy(h->aux_stream);
+  }
+  if (h->aux_event) cudaEventDestroy(h->aux_event);
   delete h;
   return INVDFT_OK;
 }
@@ -236,6 +241,7 @@ invdft_status invdft_workspace_size(invdft_handle h, size_t *bytes) {
 }
 
 invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t bytes, void *stream) {
+  if (h) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, 0);
   if (!h) return INVDFT_EINVAL;
   if (!device_ptr || bytes < h->ws_bytes) {
     h->err = "bind_workspace: workspace missing or smaller than invdft_workspace_size";

@@ -35,14 +35,25 @@ namespace {
 constexpr int kBThreads = 256;
 constexpr long long kWaitLimit = 1LL << 24;   // polls of a phase counter (with back-off)
 
+// column-quad arithmetic on packed FP32 pairs (each lane the IEEE
+// round-to-nearest operation, as in the scalar forms)
+__device__ __forceinline__ float4 f4cat(const float2 &a, const float2 &b) {
+  return make_float4(a.x, a.y, b.x, b.y);
+}
 __device__ __forceinline__ float4 f4fma(float a, const float4 &x, const float4 &y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  const float2 aa = make_float2(a, a);
+  return f4cat(__ffma2_rn(aa, make_float2(x.x, x.y), make_float2(y.x, y.y)),
+               __ffma2_rn(aa, make_float2(x.z, x.w), make_float2(y.z, y.w)));
 }
 __device__ __forceinline__ float4 f4add(const float4 &x, const float4 &y) {
-  return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  return f4cat(__fadd2_rn(make_float2(x.x, x.y), make_float2(y.x, y.y)),
+               __fadd2_rn(make_float2(x.z, x.w), make_float2(y.z, y.w)));
 }
+// x - y as x + (-1) y (exact product, one rounding)
 __device__ __forceinline__ float4 f4sub(const float4 &x, const float4 &y) {
-  return make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  return f4cat(__ffma2_rn(m1, make_float2(y.x, y.y), make_float2(x.x, x.y)),
+               __ffma2_rn(m1, make_float2(y.z, y.w), make_float2(x.z, x.w)));
 }
 
 // even / odd parts of a line of P+1 values (P even)

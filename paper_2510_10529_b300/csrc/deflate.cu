@@ -310,6 +310,13 @@ int elementwise_grid(long long n) {
 
 }  // namespace
 
+cudaError_t launch_sum_partials(const double *partial, int nblk, int n, double *out,
+                                cudaStream_t s) {
+  ::invdft::count_launch();
+  defl_sum_partials<<<(n + 31) / 32, 256, 0, s>>>(partial, nblk, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_pad_f32(const double *X, int n, int np, long long L, float *F,
                                    cudaStream_t s) {
   if (n < 1 || np < n || L < 1) return cudaErrorInvalidValue;

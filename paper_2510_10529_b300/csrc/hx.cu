@@ -298,10 +298,12 @@ cudaError_t dispatch_hx(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
 }
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
   const bool tc = uses_tc(c, a);
-  if (tc) return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + 8, s);
+  if (tc)
+    return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + kStWaitHxTc, s);
   const bool simt_q4 = c->g.p == 4 && c->cell_perm && a.ncol % 4 == 0 && a.Z != a.X &&
                        a.Z != a.W && (const void *)a.Z != (const void *)a.E;
-  if (simt_q4) return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, c->status + 9, s);
+  if (simt_q4)
+    return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, c->status + kStWaitHxSimt, s);
   return launch_hx(c->g, c->v, a, s);
 }
 

@@ -53,14 +53,29 @@ struct SmArgs {
 template <int C>
 __host__ __device__ constexpr int simt_threads() { return (25 * (C / 4) + 31) / 32 * 32; }
 
+// Column-quad arithmetic on packed FP32 pairs (one instruction per two
+// lanes; each lane is the IEEE round-to-nearest operation, so results are
+// those of the scalar forms).
+__device__ __forceinline__ float2 f4_lo(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f4_hi(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 f4_cat(const float2 &a, const float2 &b) {
+  return make_float4(a.x, a.y, b.x, b.y);
+}
 __device__ __forceinline__ float4 f4_fma(float a, const float4 &x, const float4 &y) {
-  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  const float2 aa = make_float2(a, a);
+  return f4_cat(__ffma2_rn(aa, f4_lo(x), f4_lo(y)), __ffma2_rn(aa, f4_hi(x), f4_hi(y)));
 }
 __device__ __forceinline__ float4 f4_add(const float4 &x, const float4 &y) {
-  return make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+  return f4_cat(__fadd2_rn(f4_lo(x), f4_lo(y)), __fadd2_rn(f4_hi(x), f4_hi(y)));
 }
+// x - y as x + (-1) y: the product is exact, so this is the rounded difference
 __device__ __forceinline__ float4 f4_sub(const float4 &x, const float4 &y) {
-  return make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+  const float2 m1 = make_float2(-1.f, -1.f);
+  return f4_cat(__ffma2_rn(m1, f4_lo(y), f4_lo(x)), __ffma2_rn(m1, f4_hi(y), f4_hi(x)));
+}
+__device__ __forceinline__ float4 f4_scale(float a, const float4 &x) {
+  const float2 aa = make_float2(a, a);
+  return f4_cat(__fmul2_rn(aa, f4_lo(x)), __fmul2_rn(aa, f4_hi(x)));
 }
 
 // A and B are centrosymmetric (M[i][j] = M[4-i][4-j]), so y = M u splits into
@@ -212,7 +227,7 @@ hx_simt_kernel(const __grid_constant__ SmArgs p, const __grid_constant__ CUtenso
       for (int x = 0; x < kQ; ++x) {
         const float4 r = stg[(5 * l + x) * Q4 + q];
         const float sc = dlf[buf][0][x] * syz;
-        in[x] = make_float4(sc * r.x, sc * r.y, sc * r.z, sc * r.w);
+        in[x] = f4_scale(sc, r);
         if (x < 4) {
           const int col = min(c0 + 4 * q, ncol - 4);
           nod[x] = make_float4(p.alpha * (vc[x] - sshift[col]) * r.x,
@@ -277,12 +292,9 @@ hx_simt_kernel(const __grid_constant__ SmArgs p, const __grid_constant__ CUtenso
           const uint32_t e0 = (row + x) * (uint32_t)ncol + (uint32_t)col;
           const float sc = syz * dlf[buf][0][x];
           const float4 y = u[(5 * l + x) * Q4 + q];
-          float4 o = make_float4(sc * y.x, sc * y.y, sc * y.z, sc * y.w);
+          float4 o = f4_scale(sc, y);
           if (x < 4 && own_yz) {
-            o.x += nod[x].x;
-            o.y += nod[x].y;
-            o.z += nod[x].z;
-            o.w += nod[x].w;
+            o = f4_add(o, nod[x]);
             if (HW) {
               const float4 w4 = *reinterpret_cast<const float4 *>(p.W + e0);
               o.x = fmaf(p.beta, w4.x, o.x);

@@ -20,6 +20,13 @@ constexpr int kMaxDense = 96;       // widest subspace of the one-CTA dense eige
 constexpr int kMaxGroup = 16;       // largest degenerate set handled by the projections
 constexpr int kGramBlocks = 296;    // 2 x 148 SMs: partial sums of tall-skinny reductions
 
+// Device status words of the kernels with bounded waits (non-zero: a wait gave
+// up; the solvers read them back with their convergence data)
+constexpr int kStWaitHxTc = 8;      // H~X on the tensor cores
+constexpr int kStWaitHxSimt = 9;    // H~X with TMA brick loads
+constexpr int kStWaitGram = 10;     // deflation Gram on the tensor cores
+constexpr int kStWaitCount = 3;
+
 // Geometry and 1D factors of the cell operator, passed to kernels by value.
 // K_e = kc * (B (x) B (x) A + B (x) A (x) B + A (x) B (x) B)  (z, y, x order),
 // kc = h/4, with A, B the 1D GLL stiffness and consistent mass on [-1, 1].
@@ -137,6 +144,9 @@ struct Ctx {
   double loss = 0.0, err_l2 = 0.0;
   // pinned host mirror for small read-backs
   double *hbuf = nullptr;           // 16 * kMaxCols doubles
+  int nsm = 148;                    // SMs of the device (set at bind)
+  cudaStream_t aux_stream = nullptr;  // non-blocking stream for captured work (lazy)
+  cudaEvent_t aux_event = nullptr;
 };
 
 }  // namespace invdft
@@ -250,6 +260,15 @@ cudaError_t launch_defl_gram_f32(const float *Psi, int n1p, const float *Z, int 
 cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, int n2p,
                                    long long L, float *Z, double alpha, const float *V,
                                    double *dot_out, double *partial, cudaStream_t s);
+// Tensor-core version of launch_defl_gram_f32 (deflate_tc.cu): G[n1p][n2p] =
+// Psi^T Z with two-term TF32 splitting of both operands, FP64 sums across
+// CTAs; partial holds nsm * n1p * n2p doubles; err: device word set to 4 if
+// an MMA wait gave up.
+cudaError_t launch_defl_gram_tc(const float *Psi, int n1p, const float *Z, int n2p, long long L,
+                                double *G, double *partial, int *err, int nsm, cudaStream_t s);
+// out[e] = sum_b partial[b * n + e], b < nblk
+cudaError_t launch_sum_partials(const double *partial, int nblk, int n, double *out,
+                                cudaStream_t s);
 // F[a][j] = j < n ? X[a][j] : 0 for j < np (FP64 -> FP32 with zero padding)
 cudaError_t launch_convert_pad_f32(const double *X, int n, int np, long long L, float *F,
                                    cudaStream_t s);

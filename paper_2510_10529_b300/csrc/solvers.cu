@@ -69,6 +69,19 @@ invdft_status fetch_many(Ctx *c, std::initializer_list<Piece> pieces, cudaStream
   return INVDFT_OK;
 }
 
+// A kernel whose bounded wait gave up leaves its status word set; the solvers
+// read the words back with their convergence data.
+invdft_status check_waits(Ctx *c, const int *w) {
+  static const char *const what[kStWaitCount] = {"H~X (tensor cores)", "H~X (TMA bricks)",
+                                                 "deflation Gram"};
+  for (int i = 0; i < kStWaitCount; ++i)
+    if (w[i]) {
+      c->err = std::string("a bounded device wait gave up in ") + what[i];
+      return INVDFT_ETIMEOUT;
+    }
+  return INVDFT_OK;
+}
+
 invdft_status push(Ctx *c, void *dev, const void *host, size_t bytes, cudaStream_t s) {
   // synchronous w.r.t. the host buffer: the stream is synchronised before reuse
   INV_CUDA(c, cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s));
@@ -364,11 +377,13 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
   for (;;) {
     CU(launch_occupations(c->eps, n, c->o.n_electrons, c->o.kT, c->occ, c->dfde, c->scal + kScMu,
                           c->status, s), "occupations");
-    int occ_status = 0;
+    int occ_status = 0, waits[kStWaitCount];
     TRY(fetch_many(c, {{c->eps, n * sizeof(double), theta.data()},
                        {c->occ, n * sizeof(double), occ.data()},
                        {c->scal + kScRes, n * sizeof(double), res2.data()},
-                       {c->status + 1, sizeof(int), &occ_status}}, s));
+                       {c->status + 1, sizeof(int), &occ_status},
+                       {c->status + kStWaitHxTc, sizeof(waits), waits}}, s));
+    TRY(check_waits(c, waits));
     if (occ_status) {
       c->err = "occupations: kT = 0 needs an even electron count and nstates > N_e/2";
       return INVDFT_EINVAL;
@@ -457,13 +472,17 @@ invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s
     return INVDFT_OK;
   }
   // padded FP32 blocks (Psi width a multiple of 8, Z width of 4)
-  CU(launch_defl_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
-     "gram(deflate)");
   if (no >= 16) {
+    // Gram on the tensor cores (tcgen05, both operands split into two TF32
+    // terms); update with the fused dot on the CUDA cores
+    CU(launch_defl_gram_tc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial,
+                           c->status + kStWaitGram, c->nsm, s), "gram(deflate)");
     CU(launch_defl_update_f32((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
                               (const float *)V, dot, c->partial, s), "update(deflate)");
   } else {
     // narrow blocks: one row per thread keeps every thread busy
+    CU(launch_defl_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
+       "gram(deflate)");
     CU(launch_stripe_rotate<T>(Psi, nv, Cp, no, c->L, Z, -1.0, s), "update(deflate)");
     if (V) CU(launch_coldot_f32((const float *)V, (const float *)Z, no, c->L, dot, c->partial, s), "coldot");
   }
@@ -477,6 +496,30 @@ template <typename T>
 invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int nv, const T *b,
                            T *x, const std::vector<double> &tol, int maxit, int *iters_out,
                            cudaStream_t s) {
+  // The legacy default stream cannot be captured into a graph: the solve then
+  // runs on the handle's own non-blocking stream, ordered after the caller's
+  // stream on entry and before it on every return.
+  struct Join {
+    Ctx *c;
+    cudaStream_t caller = nullptr, own = nullptr;
+    ~Join() {
+      if (own && cudaEventRecord(c->aux_event, own) == cudaSuccess)
+        cudaStreamWaitEvent(caller, c->aux_event, 0);
+    }
+  } join{c};
+  if (!c->prof.on && (s == nullptr || s == cudaStreamLegacy)) {
+    bool ok = true;
+    if (!c->aux_stream)
+      ok = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->aux_event, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && cudaEventRecord(c->aux_event, s) == cudaSuccess &&
+        cudaStreamWaitEvent(c->aux_stream, c->aux_event, 0) == cudaSuccess) {
+      join.caller = s;
+      join.own = c->aux_stream;
+      s = c->aux_stream;
+    }
+    cudaGetLastError();
+  }
   const long long L = c->L;
   const size_t blk = (size_t)L * n;
   // unnormalised Lanczos vectors qh, zh (current c, other o), w pair, H~ zh
@@ -594,7 +637,10 @@ invdft_status minres_block(Ctx *c, const AdjPlan &pl, int n, const T *Psi, int n
   if (result != INVDFT_OK) return result;
   CU(launch_mr_finish<T>(zo, wpp, wp, x, st, n, L, s), "mr_finish");
   std::vector<double> itv(n);
-  TRY(fetch(c, st + kMrIters * n, n * sizeof(double), itv.data(), s));
+  int waits[kStWaitCount];
+  TRY(fetch_many(c, {{st + kMrIters * n, n * sizeof(double), itv.data()},
+                     {c->status + kStWaitHxTc, sizeof(waits), waits}}, s));
+  TRY(check_waits(c, waits));
   int mx = 0;
   for (int j = 0; j < n; ++j) mx = std::max(mx, (int)itv[j]);
   *iters_out = mx;

@@ -245,6 +245,32 @@ def test_q4_mixed_solvers_match_oracle(prec):
     assert np.linalg.norm(g - g_ora) <= 1e-5 * np.linalg.norm(g_ora)
 
 
+def test_wide_adjoint_block_matches_oracle():
+    """36 electrons in 24 states at kT > 0 on a Q4 mesh: the adjoint MINRES
+    block is at least 16 columns wide, so its deflation runs on the tensor
+    cores (three-term TF32 splitting); loss and gradient as above."""
+    mesh = fe.Mesh(-6.0, 6.0, 4, 4)
+    xyz = mesh.coords()
+    R = np.array([[0.8, -0.3, 0.1], [-0.9, 0.4, -0.2], [0.1, 0.9, 0.6]])
+    v = W.smeared_coulomb(xyz, R, np.array([14.0, 12.0, 10.0]), 0.5)
+    bump = 0.1 * np.exp(-np.sum((xyz - 0.5) ** 2, 1))
+    Ne, nst, kT = 36.0, 24, W.KT_DEFAULT
+    rho_d = ks.forward(mesh, v + bump, Ne, nst, kT)["rho"]
+    op = inverse.Problem(mesh=mesh, v_fixed=v, rho_data=rho_d, w=np.ones(mesh.L),
+                         n_electrons=Ne, nstates=nst, kT=kT)
+    v_xc = 0.5 * bump
+    L_ora, e_ora, g_ora, fw_ora = inverse.evaluate(op, v_xc)
+    pb = _problem(-6.0, 6.0, 4, 4, nstates=nst, n_electrons=Ne, kT=kT, prec="mixed",
+                  eig_tol=1e-10, adj_tol=1e-11, cheb_degree=20)
+    pb.set_potential(_cuda(v), _cuda(v_xc))
+    loss, g, st = pb.loss_grad(_cuda(rho_d), _cuda(np.ones(mesh.L)))
+    g = g.cpu().numpy()
+    err = np.linalg.norm(g - g_ora) / np.linalg.norm(g_ora)
+    print(f"wide adjoint block: loss rel {abs(loss - L_ora) / L_ora:.2e}, grad rel {err:.2e}")
+    assert abs(loss - L_ora) <= 1e-8 * L_ora
+    assert err <= 1e-5
+
+
 def test_profile_hx_counts_each_kernel_kind():
     """The per-launch H~X timing of the instrumentation entry point sorts the
     launches into FP64, FP32 CUDA-core and TF32 tensor-core kinds."""
