@@ -1,14 +1,15 @@
 // Deflation Gram of the FP32 MINRES blocks on the tensor cores (Sec. 3.2.2):
 //   C = Psi^T Z,   Psi [L][n1p] (deflation vectors), Z [L][n2p] (MINRES block)
-// as tcgen05 kind::tf32 MMAs, one 64-node tile = one K extent of 64, with
+// as tcgen05 kind::tf32 MMAs, one 32-node tile = one K extent of 32, with
 // TF32 splitting of both operands: x = hi + lo, hi the TF32 rounding of x and
 // lo = x - hi (exact in FP32; the MMA takes its TF32 part).  The A operand
 // stacks the hi rows (0..63) over the lo rows (64..127) of Psi^T, and two
 // MMAs per K-step (B = Z_hi, then Z_lo) accumulate all four split products
 // in TMEM: C = D[0:64] + D[64:128], summed in FP64 across CTAs.
 //
-// Persistent CTAs (one per SM) walk the tiles.  Psi and Z rows are staged
-// node-major by 16-byte cp.async, two tiles ahead, and transposed into the
+// Persistent CTAs (two per SM, so that the barrier-separated phases of one
+// overlap those of the other) walk 32-node tiles.  Psi and Z rows are staged
+// node-major by 16-byte cp.async, one tile ahead, and transposed into the
 // K-major no-swizzle operand layout by the threads that split them; the
 // operand buffers are double-buffered so that the MMAs of a tile overlap the
 // split of the next.  Waits on the MMA barriers are bounded: a wait that
@@ -75,9 +76,10 @@ __device__ __forceinline__ void cp16(void *dst, const void *src) {
 
 // ---------------------------------------------------------------------------
 // Gram C = Psi^T Z (partials per CTA), tensor cores
-constexpr int kGK = 64;     // nodes per tile = MMA K extent of a tile
-constexpr int kGThreads = 512;
+constexpr int kGK = 32;     // nodes per tile = MMA K extent of a tile
+constexpr int kGThreads = 256;
 constexpr int kGWarps = kGThreads / 32;
+constexpr int kGPerSm = 2;  // resident CTAs per SM: one CTA's barrier phases overlap the other's
 
 struct TcGram {
   const float *Psi;
@@ -89,9 +91,9 @@ struct TcGram {
 };
 
 constexpr int kGLd = 64;    // staging row stride (floats) of both Psi and Z
-constexpr int kGStages = 3; // staging ring: loads run two tiles ahead
+constexpr int kGStages = 2; // staging ring: loads run one tile ahead
 
-__global__ void __launch_bounds__(kGThreads, 1) defl_gram_tc_kernel(const TcGram p) {
+__global__ void __launch_bounds__(kGThreads, kGPerSm) defl_gram_tc_kernel(const TcGram p) {
   extern __shared__ __align__(1024) unsigned char gsm[];
   constexpr uint32_t szA = kTM * kGK * 4, szB = kTN * kGK * 4, szOp = szA + 2 * szB;
   float *raw = reinterpret_cast<float *>(gsm + 2 * szOp);
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kGThreads, 1) defl_gram_tc_kernel(const TcGram
     const float *stage = raw + st * rawsz;
     unsigned char *A = gsm + ob * szOp;
     for (int u = warp; u < ncg * (kGK / 16); u += kGWarps) {
-      const int cgi = u >> 2, nb = (u & 3) * 16;
+      const int cgi = u / (kGK / 16), nb = (u % (kGK / 16)) * 16;
       const bool psi = cgi < cg1;
       const int col = (psi ? cgi : cgi - cg1) * 32 + lane;
       if (col >= (psi ? p.n1p : p.n2p)) continue;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kGThreads, 1) defl_gram_tc_kernel(const TcGram
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     }
-    double *red = reinterpret_cast<double *>(raw);     // [64][65]
+    double *red = reinterpret_cast<double *>(gsm);     // [64][65], in the operand buffers
     const int m = (g & 1) * 32 + lane;
     if (rd && g < 2) {
 #pragma unroll
@@ -291,11 +293,12 @@ __global__ void __launch_bounds__(kGThreads, 1) defl_gram_tc_kernel(const TcGram
 size_t defl_gram_tc_smem() {
   const size_t ops = 2 * (size_t)(kTM * kGK + 2 * kTN * kGK) * 4;
   const size_t raw = kGStages * (size_t)(2 * kGK * kGLd) * 4;
-  return ops + std::max(raw, (size_t)64 * 65 * 8);
+  static_assert(2 * (kTM * kGK + 2 * kTN * kGK) * 4 >= 64 * 65 * 8, "reduction buffer");
+  return ops + raw;
 }
 
 // G = Psi^T Z (FP32-accurate, summed in FP64 across CTAs); n1p a multiple of 8
-// (<= 64), n2p a multiple of 4 (<= 64); partial holds nsm * n1p * n2p doubles.
+// (<= 64), n2p a multiple of 4 (<= 64); partial holds 2 nsm * n1p * n2p doubles.
 cudaError_t launch_defl_gram_tc(const float *Psi, int n1p, const float *Z, int n2p, long long L,
                                 double *G, double *partial, int *err, int nsm, cudaStream_t s) {
   if (n1p < 8 || n1p > 64 || n1p % 8 != 0 || n2p < 4 || n2p > 64 || n2p % 4 != 0 || L < 1)
@@ -312,7 +315,7 @@ cudaError_t launch_defl_gram_tc(const float *Psi, int n1p, const float *Z, int n
   p.n2p = n2p;
   p.L = L;
   const long long ntile = (L + kGK - 1) / kGK;
-  const int grid = (int)std::min<long long>(ntile, nsm);
+  const int grid = (int)std::min<long long>(ntile, (long long)kGPerSm * nsm);
   ::invdft::count_launch();
   defl_gram_tc_kernel<<<grid, kGThreads, smem, s>>>(p);
   e = cudaGetLastError();

@@ -262,7 +262,7 @@ cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, i
                                    double *dot_out, double *partial, cudaStream_t s);
 // Tensor-core version of launch_defl_gram_f32 (deflate_tc.cu): G[n1p][n2p] =
 // Psi^T Z with two-term TF32 splitting of both operands, FP64 sums across
-// CTAs; partial holds nsm * n1p * n2p doubles; err: device word set to 4 if
+// CTAs; partial holds 2 nsm * n1p * n2p doubles; err: device word set to 4 if
 // an MMA wait gave up.
 cudaError_t launch_defl_gram_tc(const float *Psi, int n1p, const float *Z, int n2p, long long L,
                                 double *G, double *partial, int *err, int nsm, cudaStream_t s);
