@@ -50,10 +50,10 @@ METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 # DRAM bytes per (node, column) of one FP32 CUDA-core H~X launch: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of hx_simt_kernel<64, 0> (TMA
 # brick version) on the 24^3-cell Q4 mesh (857,375 unknowns) with 60 columns,
-# 485.69 + 191.43 MB, plus the 4-byte zero fill of Z that precedes the kernel
+# 486.90 + 190.83 MB, plus the 4-byte zero fill of Z that precedes the kernel
 # in the same launch.  Traffic grows with unknowns x columns, so the in-step
 # figure scales by them.
-HX_SIMT_DRAM_BYTES_PER_NODE_COL = (485.69e6 + 191.43e6) / (857375 * 60) + 4.0
+HX_SIMT_DRAM_BYTES_PER_NODE_COL = (486.90e6 + 190.83e6) / (857375 * 60) + 4.0
 
 # H~X column-applications per inverse iteration on each workload, as counted by
 # the GPU path (line-search solves, Chebyshev passes, MINRES iterations) over the
