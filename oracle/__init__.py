@@ -21,6 +21,9 @@ Modules and the passages of the paper they follow:
   lbfgs       limited-memory BFGS update of v_xc (Eq. 21).
   chebyshev   scalar Chebyshev recurrences used by the filter (Sec. 3.2.2).
   scf         self-consistent generation of a target density (input recipe).
+  initial_guess  initial v_xc of Eq. 25 and Eq. 26: Slater or LB94 exchange plus
+              PW92 correlation, blended with the scaled Fermi-Amaldi potential
+              (Sec. 4.2.3); nodal density gradients of the FE interpolant.
 
 Parity status of each function is stated in its docstring; every function has
 at least one pin in tests/test_oracle_*.py (closed forms, brute force,
