@@ -21,6 +21,9 @@ Modules and the passages of the paper they follow:
   lbfgs       limited-memory BFGS update of v_xc (Eq. 21).
   chebyshev   scalar Chebyshev recurrences used by the filter (Sec. 3.2.2).
   scf         self-consistent generation of a target density (input recipe).
+  graded      graded tensor-product meshes (Sec. 4.2.2 reading): per-axis cell
+              breaks refined towards the nuclei, per-cell scalars on the three
+              Kronecker terms of K_e (Eq. 17), element orders up to 6.
   initial_guess  initial v_xc of Eq. 25 and Eq. 26: Slater or LB94 exchange plus
               PW92 correlation, blended with the scaled Fermi-Amaldi potential
               (Sec. 4.2.3); nodal density gradients of the FE interpolant.
