@@ -24,6 +24,8 @@ Modules and the passages of the paper they follow:
   graded      graded tensor-product meshes (Sec. 4.2.2 reading): per-axis cell
               breaks refined towards the nuclei, per-cell scalars on the three
               Kronecker terms of K_e (Eq. 17), element orders up to 6.
+  potential_matrix  dense per-cell potential matrices: the Gauss-quadrature
+              reading of the potential term of Eq. 17 (the default collocates it).
   initial_guess  initial v_xc of Eq. 25 and Eq. 26: Slater or LB94 exchange plus
               PW92 correlation, blended with the scaled Fermi-Amaldi potential
               (Sec. 4.2.3); nodal density gradients of the FE interpolant.
