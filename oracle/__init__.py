@@ -26,6 +26,8 @@ Modules and the passages of the paper they follow:
               Kronecker terms of K_e (Eq. 17), element orders up to 6.
   potential_matrix  dense per-cell potential matrices: the Gauss-quadrature
               reading of the potential term of Eq. 17 (the default collocates it).
+  transfer    linear (Q1) v_xc mesh, transfer of v_xc to the orbital nodes and of
+              the gradient back (Sec. 3.1.1, Sec. 3.2.2, Eq. 22).
   initial_guess  initial v_xc of Eq. 25 and Eq. 26: Slater or LB94 exchange plus
               PW92 correlation, blended with the scaled Fermi-Amaldi potential
               (Sec. 4.2.3); nodal density gradients of the FE interpolant.
