@@ -395,6 +395,10 @@ def run_ours(args, rank, world):
                        "cheb_passes": [s["cheb_passes"] for s in stats],
                        "minres_iters": [s["minres_iters_max"] for s in stats],
                        "ls_trials": [s["ls_trials"] for s in stats],
+                       # host wall time of the forward solves (all line-search
+                       # trials) and of the adjoint solve of each step
+                       "t_forward_ms": [s["t_forward_ms"] for s in stats],
+                       "t_adjoint_ms": [s["t_adjoint_ms"] for s in stats],
                        "col_applies_per_step": col_applies / args.steps,
                        "hx_ms_share": sum(prof[k]["ms"] for k in ("fp64", "fp32", "tf32"))
                        / (ms_max * args.steps),
