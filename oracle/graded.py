@@ -160,6 +160,38 @@ class GradedMesh:
         Y = d[:, None] * self.apply_K(d[:, None] * X2) + v[:, None] * X2
         return Y.ravel() if squeeze else Y
 
+    def axis_matrices(self):
+        """Assembled 1D matrices of each axis over its interior nodes:
+        Ad = sum_e (2 / h_e) A and Bd = sum_e (h_e / 2) B (dense, small)."""
+        out = []
+        for h, N in zip(self.h, self.N):
+            Ad, Bd = np.zeros((N, N)), np.zeros((N, N))
+            for e in range(len(h)):
+                sl = slice(e * self.p, e * self.p + self.q)
+                Ad[sl, sl] += (2.0 / h[e]) * self.A1
+                Bd[sl, sl] += (0.5 * h[e]) * self.B1
+            out.append((Ad[1:-1, 1:-1], Bd[1:-1, 1:-1]))
+        return out
+
+    def apply_K_sweeps(self, X: np.ndarray) -> np.ndarray:
+        """K X by 1D sweeps of the assembled axis matrices.  The cell scalars
+        separate by axis (c_x = (2/h_x)(h_y/2)(h_z/2) and cyclic), and the cells
+        form a product set, so the assembled K is itself a sum of Kronecker
+        products:  K = 1/2 [B_z (x) B_y (x) A_x + B_z (x) A_y (x) B_x
+        + A_z (x) B_y (x) B_x]  over the interior nodes.  Seven sweeps:
+        P = A_x X, Q = B_x X;  R = B_y P + A_y Q, S = B_y Q;  K X = (B_z R + A_z S) / 2."""
+        (Ax, Bx), (Ay, By), (Az, Bz) = self.axis_matrices()
+        nx, ny, nz = self.Ni
+        squeeze = X.ndim == 1
+        X4 = X.reshape(nz, ny, nx, -1)
+        P = np.einsum("ia,zyan->zyin", Ax, X4)
+        Q = np.einsum("ia,zyan->zyin", Bx, X4)
+        R = np.einsum("ja,zaxn->zjxn", By, P) + np.einsum("ja,zaxn->zjxn", Ay, Q)
+        S = np.einsum("ja,zaxn->zjxn", By, Q)
+        Y = 0.5 * (np.einsum("ka,ayxn->kyxn", Bz, R) + np.einsum("ka,ayxn->kyxn", Az, S))
+        Y = Y.reshape(self.L, -1)
+        return Y.ravel() if squeeze else Y
+
     def assemble_K(self) -> sp.csr_matrix:
         """Sparse K over the interior nodes, cell by cell (small meshes)."""
         p, q = self.p, self.q

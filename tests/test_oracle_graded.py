@@ -118,3 +118,17 @@ def test_graded_breaks_follow_the_target_size():
     S_lin = 2.0 * np.log(hout / hin) / g        # both sides of the centre, inside d1
     S = S_lin + ((0.5 - d1 - lo) + (hi - 0.5 - d1)) / hout
     np.testing.assert_allclose(np.median(ratio), S / n, rtol=0.02)
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_assembled_operator_is_a_sum_of_kronecker_products(p):
+    # the cell-by-cell K (Eq. 17 assembly) equals seven sweeps of the assembled
+    # 1D axis matrices, on equal and on graded breaks
+    for bx, by, bz in ([np.linspace(-3.0, 3.0, 4)] * 3, _graded(p, n=4, lo=-3.0, hi=3.0, seed=3)):
+        g = GradedMesh(bx, by, bz, p)
+        X = np.random.default_rng(4).standard_normal((g.L, 2))
+        np.testing.assert_allclose(g.apply_K_sweeps(X), g.apply_K(X), rtol=1e-12, atol=1e-12)
+    ref = fe.Mesh(-3.0, 3.0, 3, p)
+    g = GradedMesh(*([np.linspace(-3.0, 3.0, 4)] * 3), p)
+    X = np.random.default_rng(5).standard_normal((ref.L, 3))
+    np.testing.assert_allclose(g.apply_K_sweeps(X), ref.apply_K(X), rtol=1e-12, atol=1e-12)
