@@ -79,3 +79,20 @@ def test_occupations_and_electron_count(kT):
             fp = 2.0 / (1.0 + np.exp((e2[i] - mu) / kT))
             fm = 2.0 / (1.0 + np.exp((e1[i] - mu) / kT))
             assert abs((fp - fm) / (2 * h) - fw["dfde"][i]) < 1e-5 * max(1.0, abs(fw["dfde"][i]))
+
+
+def test_zero_temperature_mu_is_the_limit_of_the_finite_temperature_one():
+    # a gapped spectrum: as kT -> 0 the bisection's mu tends to mid-gap (equal
+    # hole and electron tails at the band edges), which is the kT = 0
+    # convention of the closed-shell branch.  Temperatures stay above ~gap/40:
+    # below that every mu in the gap gives sum f = N_e to machine precision.
+    eps = np.array([-2.0, -1.3, -1.25, -0.4, 0.1, 0.7])
+    _, _, mu0 = ks.occupations(eps, 6.0, 0.0)
+    dev = []
+    for kT in (0.05, 0.03, 0.02):
+        f, _, mu = ks.occupations(eps, 6.0, kT)
+        assert abs(f.sum() - 6.0) < 1e-12
+        dev.append(abs(mu - mu0))
+        assert dev[-1] < 0.5 * kT
+    assert dev[0] > dev[1] > dev[2]
+    assert abs(mu0 - 0.5 * (-1.25 - 0.4)) < 1e-15
