@@ -39,6 +39,11 @@
  * ABI.  On failure the text of the last error is available from
  * invdft_last_error(handle) (or invdft_last_error(NULL) for failures before a
  * handle exists).  INVDFT_ENOCONV leaves valid, flagged results.
+ * INVDFT_ETIMEOUT is reported by the solves that read back the kernels' wait
+ * status words (forward solve, adjoint MINRES, batch step): a kernel whose
+ * bounded wait gave up set its word and left early, so the results of that
+ * call are not valid.  The words stay set for the handle, so every later
+ * solve on it reports the error again; destroy the handle after it.
  *
  * Threading: a handle is not thread safe; distinct handles are independent.
  */
