@@ -241,12 +241,12 @@ invdft_status invdft_workspace_size(invdft_handle h, size_t *bytes) {
 }
 
 invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t bytes, void *stream) {
-  if (h) cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, 0);
   if (!h) return INVDFT_EINVAL;
   if (!device_ptr || bytes < h->ws_bytes) {
     h->err = "bind_workspace: workspace missing or smaller than invdft_workspace_size";
     return INVDFT_ENOMEM;
   }
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, 0);
   cudaStream_t s = (cudaStream_t)stream;
   char *base = reinterpret_cast<char *>(((uintptr_t)device_ptr + 255) & ~uintptr_t(255));
   if ((size_t)(base - (char *)device_ptr) + h->ws_bytes - 256 > bytes) {

@@ -59,3 +59,50 @@ def test_create_rejects_bad_arguments():
         P.invdft_create_mesh(P.MeshDesc(lo=0.0, hi=1.0, ncell=2, order=2), P.Opts(nstates=0))
     with pytest.raises(P.InvdftError):
         P.invdft_create_mesh(P.MeshDesc(lo=1.0, hi=0.0, ncell=2, order=2), P.Opts(nstates=2))
+
+
+def test_device_calls_validate_on_the_host_first():
+    """Every device-facing call checks its handle and arguments on the host
+    before any CUDA call: on a handle without a bound workspace (or with null
+    arguments) it returns an error code and leaves a message, so this runs
+    without a GPU.  The non-null pointers below are never dereferenced."""
+    import paper_2510_10529_b300 as P
+    from paper_2510_10529_b300._lib import INVDFT_EINVAL, INVDFT_ENOMEM, lib
+    h, L = P.invdft_create_mesh(P.MeshDesc(lo=-4.0, hi=4.0, ncell=2, order=2),
+                                P.Opts(nstates=2, n_electrons=2.0))
+    fake = C.c_void_p(0x1000)
+    st = P.Stats()
+    loss = C.c_double()
+    try:
+        calls = {
+            "bind_workspace": lambda: lib.invdft_bind_workspace(h, None, 0, None),
+            "mass_diag": lambda: lib.invdft_mass_diag(h, fake, None),
+            "set_potential": lambda: lib.invdft_set_potential(h, fake, None, None),
+            "apply_h": lambda: lib.invdft_apply_h(h, fake, C.c_void_p(0x2000), 4,
+                                                  P.INVDFT_FP64, None),
+            "apply_h aliasing": lambda: lib.invdft_apply_h(h, fake, fake, 4, P.INVDFT_FP64, None),
+            "chebyshev_filter": lambda: lib.invdft_chebyshev_filter(
+                h, fake, C.c_void_p(0x2000), 2, 8, 0.0, 1.0, -1.0, P.INVDFT_FP64, None),
+            "forward_solve": lambda: lib.invdft_forward_solve(h, None, None, None, None,
+                                                              C.byref(st), None),
+            "adjoint_solve": lambda: lib.invdft_adjoint_solve(h, fake, None, C.byref(st), None),
+            "density_vjp": lambda: lib.invdft_density_vjp(h, fake, fake, C.byref(st), None),
+            "loss_grad": lambda: lib.invdft_loss_grad(h, fake, fake, C.byref(loss), fake,
+                                                      C.byref(st), None),
+            "step": lambda: lib.invdft_step(h, fake, fake, fake, C.byref(st), None),
+        }
+        for name, call in calls.items():
+            code = call()
+            assert code in (INVDFT_EINVAL, INVDFT_ENOMEM), (name, code)
+            assert lib.invdft_last_error(h), name
+        # null arguments are rejected before the handle's state is looked at
+        assert lib.invdft_adjoint_solve(h, None, None, None, None) == INVDFT_EINVAL
+        assert lib.invdft_step(h, fake, None, fake, None, None) == INVDFT_EINVAL
+        assert lib.invdft_apply_h(None, fake, fake, 4, P.INVDFT_FP64, None) == INVDFT_EINVAL
+        # a batch needs bound mixed-precision problems
+        arr = (C.c_void_p * 1)(h.value)
+        out = C.c_void_p()
+        assert lib.invdft_batch_create(arr, 1, C.byref(out)) == INVDFT_EINVAL
+        assert lib.invdft_batch_create(None, 1, C.byref(out)) == INVDFT_EINVAL
+    finally:
+        P.invdft_destroy(h)
