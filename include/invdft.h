@@ -260,9 +260,9 @@ invdft_status invdft_graph_stats(long long *out3);
  * because an allocation would synchronise the device in the middle of its
  * pipeline), or a caller that simply has no workspace to bind.  It computes,
  * like the reduction inside invdft_loss_grad,
- *   out3[0] = sum_a m_a w_a (rho_data_a - rho_a)^2   (the loss, Eq. 1),
- *   out3[1] = sum_a m_a (rho_data_a - rho_a)^2       (e_L2^2, Sec. 4.2.4),
- *   out3[2] = sum_a m_a rho_a                        (N_e, Eq. 5),
+ *   out3[0] = sum_a m_a w_a (rho_data_a - rho_a)^2   (the weighted loss),
+ *   out3[1] = sum_a m_a (rho_data_a - rho_a)^2       (the squared L2 error),
+ *   out3[2] = sum_a m_a rho_a                        (the electron count),
  * and, if dLdrho != NULL, dLdrho_a = -2 m_a w_a (rho_data_a - rho_a).
  * All arrays are device arrays of length L (out3: 3 doubles) owned by the
  * caller; w may be NULL (w = 1).  No handle is needed.

@@ -158,3 +158,41 @@ def test_htilde_standard_form():
     H = mesh.assemble_K().toarray() + np.diag(m * v)
     Ht = np.diag(m ** -0.5) @ H @ np.diag(m ** -0.5)
     np.testing.assert_allclose(mesh.apply_Htilde(v, X), Ht @ X, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("n,p", [(2, 4), (3, 2), (3, 4)])
+def test_htilde_rows_every_row(n, p):
+    """The row-wise definition of (H~X)_a (Eq. 17, 19), used to check sampled
+    rows of large meshes, against the separable closed form on every row:
+    with D = d1 (x) d1 (x) d1, D x is separable when x is, so
+    H~ x = D K (D x) + v o x follows from the 1D assembled K1, B1 above.
+    Every row is taken, so nodes inside cells, on faces, edges and vertices,
+    and next to the Dirichlet boundary are all covered."""
+    mesh = fe.Mesh(-1.0, 2.0, n, p)
+    A, B, _ = fe.reference_matrices(p)
+    s = 0.5 * mesh.h
+    K1 = _assembled_1d(mesh, A / s)
+    B1 = _assembled_1d(mesh, B * s)
+    d1 = mesh.m1[1:-1] ** -0.5
+    rng = np.random.default_rng(17)
+    v = rng.standard_normal(mesh.L)
+    X = np.zeros((mesh.L, 2))
+    Y = np.zeros((mesh.L, 2))
+    for col in range(2):
+        for _ in range(3):
+            a, b, c = (rng.standard_normal(mesh.Ni) for _ in range(3))
+            x = np.einsum("k,j,i->kji", c, b, a).ravel()
+            da, db, dc = d1 * a, d1 * b, d1 * c
+            kx = 0.5 * (np.einsum("k,j,i->kji", B1 @ dc, B1 @ db, K1 @ da)
+                        + np.einsum("k,j,i->kji", B1 @ dc, K1 @ db, B1 @ da)
+                        + np.einsum("k,j,i->kji", K1 @ dc, B1 @ db, B1 @ da)).ravel()
+            d = np.einsum("k,j,i->kji", d1, d1, d1).ravel()
+            X[:, col] += x
+            Y[:, col] += d * kx
+        Y[:, col] += v * X[:, col]
+    rows = np.arange(mesh.L)
+    got = fe.htilde_rows(mesh, v, rows, lambda idx: X[idx])
+    scale = np.abs(Y).max()
+    assert np.abs(got - Y).max() < 1e-13 * scale
+    # and the same rows of the assembled sparse operator
+    np.testing.assert_allclose(got, mesh.assemble_Htilde(v) @ X, rtol=0, atol=1e-13 * scale)

@@ -7,7 +7,9 @@ a fixed array inside the library.  This test calls it through the C ABI twice
 in a row on the density of a forward solve and checks loss, e_L2^2 and N_e
 against what invdft_loss_grad reports for the same potential (the two
 forward solves agree to the eigen tolerance, hence the 1e-8 bound used by the
-other loss tests).  It lives in its own file, collected last.
+other loss tests), and loss and e_L2^2 against the FP64 oracle's quadrature of
+the same density (only the summation order differs).  It lives in its own
+file, collected last.
 """
 import ctypes as C
 
@@ -22,7 +24,7 @@ def test_noalloc_loss_matches_loss_grad_twice():
     import paper_2510_10529_b300 as P
     from paper_2510_10529_b300._lib import lib
     import workloads as W
-    from oracle import fe, scf
+    from oracle import adjoint as oadj, fe, scf
 
     wl = W.cube8_q2_he()
     mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
@@ -52,6 +54,11 @@ def test_noalloc_loss_matches_loss_grad_twice():
         assert abs(o[0] - loss_ref) <= 1e-8 * loss_ref
         assert abs(o[1] - st["err_l2"] ** 2) <= 1e-8 * st["err_l2"] ** 2
         assert abs(o[2] - wl.n_electrons) <= 1e-10 * wl.n_electrons
+        # the same sums from the FP64 oracle on the same density
+        lo_ora, el_ora = oadj.loss_and_error(mesh, rho.cpu().numpy(), d["rho_data"],
+                                             w.cpu().numpy())
+        assert abs(o[0] - lo_ora) <= 1e-12 * lo_ora
+        assert abs(o[1] - el_ora ** 2) <= 1e-12 * el_ora ** 2
         g_ref = -2.0 * m * w * (rd - rho)
         assert torch.allclose(g, g_ref, rtol=1e-13, atol=0.0)
         outs.append(o)
