@@ -42,8 +42,10 @@
  * INVDFT_ETIMEOUT is reported by the solves that read back the kernels' wait
  * status words (forward solve, adjoint MINRES, batch step): a kernel whose
  * bounded wait gave up set its word and left early, so the results of that
- * call are not valid.  The words stay set for the handle, so every later
- * solve on it reports the error again; destroy the handle after it.
+ * call are not valid.  The words of the H~X and Gram kernels stay set for
+ * the handle, so every later solve on it reports the error again; destroy
+ * the handle after it.  The batch kernel's word is cleared at each launch
+ * (invdft_batch_set_wait_limit).
  *
  * Threading: a handle is not thread safe; distinct handles are independent.
  */
@@ -234,22 +236,55 @@ invdft_status invdft_batch_step(invdft_batch batch, const double *const *rho_dat
                                 const double *const *w_dev, double *const *v_xc_dev,
                                 invdft_stats *stats, invdft_status *status, void *stream);
 invdft_status invdft_batch_info(invdft_batch batch, int *chunk_cols, double *info4);
+/* invdft_batch_set_wait_limit: the persistent filter kernel waits for the
+ * previous phase of a problem by polling its phase counter, with a back-off
+ * of 256 ns per poll, and gives up after `polls` polls: it sets its error
+ * word, every CTA leaves, and the step returns INVDFT_ETIMEOUT for the
+ * problems of that launch (the results of that step are not valid).
+ * polls < 0 restores the default of 2^24 polls (seconds); polls = 0 makes
+ * the first wait for a previous phase give up at once, whether that phase is
+ * complete or not.  A zero or small limit makes a wait run out without any
+ * device fault, which is how the timeout path is tested.  Call it between
+ * steps.  EINVAL for a NULL batch, ECUDA if the limit cannot be copied to
+ * the device.                                                               */
+invdft_status invdft_batch_set_wait_limit(invdft_batch batch, int polls);
 
 /* Instrumentation for benchmarks (no counterpart in the paper).
  * invdft_profile_hx: while enabled, every H~X launch of this handle is
  * bracketed by CUDA events on its stream.  Each call first drains pending
- * events (synchronising on them) and, if out12 != NULL, writes the totals
- * since the last enable: out12[0..3] = FP64 {device ms, algorithmic bytes
+ * events (synchronising on them) and, if out16 != NULL, writes the totals
+ * since the last enable: out16[0..3] = FP64 {device ms, algorithmic bytes
  * (X and v read, Z written, plus W/E when present), nominal dense-cell
- * flops 2 (p+1)^6 ncol ncell^3, launches}, out12[4..7] the same for FP32
- * blocks on the CUDA cores, out12[8..11] for FP32 blocks on the TF32
- * tensor-core kernel.
+ * flops 2 (p+1)^6 ncol ncell^3, launches}, out16[4..7] the same for FP32
+ * launches on the CUDA cores that carry the Chebyshev filter's W or E terms,
+ * out16[8..11] for the other FP32 CUDA-core launches (the MINRES operator),
+ * out16[12..15] for FP32 blocks on the TF32 tensor-core kernel.
  * enable = 1 resets the totals and turns timing on; 0 turns it off.
  * invdft_kernel_launches: process-wide count of kernels launched by this
  * library since it was loaded (kernels run by CUDA-graph replays included).
  * invdft_graph_stats: out3 = {graphs captured, graph replays, captures the
  * runtime refused (the work then ran as plain launches)}, process-wide.     */
-invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12);
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16);
+
+/* Tuning of H~X (no counterpart in the paper).  On orders 2 and 4, FP32 and
+ * FP64 blocks whose rows are a multiple of 16 bytes run in the sweep form: a
+ * CTA owns a column of nodes of the x-y plane and a chunk of columns, and
+ * walks a segment of the z range.  Several tile variants exist (columns per
+ * CTA, tile height, planes in flight, x-cells per task).
+ * invdft_tune_hx: variant >= 0 fixes the tile variant, seglen > 0 the segment
+ * length (in cells) for every later H~X launch of this handle; -1 / 0 leave
+ * them to the autotuner, which on the first launch of each (precision, ncol,
+ * epilogue) on meshes of at least 2^18 unknowns (not while the stream is
+ * being captured) times every variant with the whole z range, halves and
+ * quarters and keeps the fastest.  nvariants (optional, host int[2])
+ * receives the number of FP32 and FP64 variants for this mesh order.  EINVAL
+ * for a NULL handle, seglen < 0 or a variant out of range.
+ * invdft_hx_config: the autotuned (variant, seglen) of this handle for a
+ * width ncol and precision (fp64 != 0: FP64), for the four epilogues
+ * {plain, E only, W only, W and E}: variant_seglen (host int[8]), -1 where
+ * that configuration has not been tuned.                                     */
+invdft_status invdft_tune_hx(invdft_handle h, int variant, int seglen, int *nvariants);
+invdft_status invdft_hx_config(invdft_handle h, int ncol, int fp64, int *variant_seglen);
 invdft_status invdft_kernel_launches(unsigned long long *count);
 invdft_status invdft_graph_stats(long long *out3);
 

@@ -145,12 +145,30 @@ def invdft_reset(h):
 
 
 def invdft_profile_hx(h, enable: bool):
-    out = np.zeros(12)
+    """H~X launch totals by kind: fp64, fp32_filter (FP32 with the filter's
+    W / E terms), fp32 (other FP32 launches: the MINRES operator), tf32."""
+    out = np.zeros(16)
     _ok("invdft_profile_hx", lib.invdft_profile_hx(h, int(enable), out.ctypes.data_as(C.c_void_p)),
         h, False)
     keys = ("ms", "bytes", "flops", "launches")
-    return {"fp64": dict(zip(keys, out[:4])), "fp32": dict(zip(keys, out[4:8])),
-            "tf32": dict(zip(keys, out[8:]))}
+    return {"fp64": dict(zip(keys, out[:4])), "fp32_filter": dict(zip(keys, out[4:8])),
+            "fp32": dict(zip(keys, out[8:12])), "tf32": dict(zip(keys, out[12:]))}
+
+
+def invdft_tune_hx(h, variant: int = -1, seglen: int = 0):
+    """Fix the tile variant (-1: autotuned) and z-segment length (0: autotuned)
+    of the sweep H~X; returns the number of FP32 and FP64 variants."""
+    n = (C.c_int * 2)()
+    _ok("invdft_tune_hx", lib.invdft_tune_hx(h, int(variant), int(seglen), n), h, False)
+    return int(n[0]), int(n[1])
+
+
+def invdft_hx_config(h, ncol: int, fp64: bool):
+    """Autotuned (variant, seglen) per epilogue {plain, E, W, W+E} (-1: not tuned)."""
+    out = (C.c_int * 8)()
+    _ok("invdft_hx_config", lib.invdft_hx_config(h, int(ncol), int(bool(fp64)), out), h, False)
+    names = ("plain", "E", "W", "WE")
+    return {names[k]: (int(out[2 * k]), int(out[2 * k + 1])) for k in range(4)}
 
 
 def invdft_graph_stats() -> dict:
@@ -272,6 +290,12 @@ class Problem:
     def profile_hx(self, enable: bool):
         return invdft_profile_hx(self.h, enable)
 
+    def tune_hx(self, variant: int = -1, seglen: int = 0):
+        return invdft_tune_hx(self.h, variant, seglen)
+
+    def hx_config(self, ncol: int, fp64: bool = False):
+        return invdft_hx_config(self.h, ncol, fp64)
+
 
 def invdft_batch_create(handles) -> int:
     arr = (C.c_void_p * len(handles))(*handles)
@@ -303,6 +327,12 @@ class Batch:
     def __init__(self, problems):
         self.problems = list(problems)
         self.h = invdft_batch_create([p.h for p in self.problems])
+
+    def set_wait_limit(self, polls: int):
+        """Polls before a phase wait of the persistent kernel gives up (0: at the
+        first wait; < 0: the default)."""
+        _ok("invdft_batch_set_wait_limit", lib.invdft_batch_set_wait_limit(self.h, int(polls)),
+            None, False)
 
     def step(self, rho_data, w, v_xc):
         stats, status = invdft_batch_step(self.h, [p.h for p in self.problems], rho_data, w,

@@ -79,6 +79,8 @@ def _load():
         "invdft_step": [H, P, P, P, C.POINTER(Stats), P],
         "invdft_reset": [H],
         "invdft_profile_hx": [H, C.c_int, P],
+        "invdft_tune_hx": [H, C.c_int, C.c_int, P],
+        "invdft_hx_config": [H, C.c_int, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
         "invdft_graph_stats": [P],
         "invdft_loss_reduce_noalloc": [P, P, P, P, C.c_longlong, P, P, P],
@@ -86,6 +88,7 @@ def _load():
         "invdft_batch_destroy": [H],
         "invdft_batch_step": [H, P, P, P, C.POINTER(Stats), P, P],
         "invdft_batch_info": [H, P, P],
+        "invdft_batch_set_wait_limit": [H, C.c_int],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -214,6 +214,14 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
     g.A[i] = c->tab.A[i];
     g.B[i] = c->tab.B[i];
   }
+  for (int ax = 0; ax < 3; ++ax) {
+    const double sh = 0.5 * (mesh->hi - mesh->lo) / mesh->ncell;
+    g.s[ax] = sh;
+    for (int i = 0; i <= g.p; ++i) {
+      const double m = (i == 0 || i == g.p) ? 2.0 * sh * c->tab.gll_w[0] : sh * c->tab.gll_w[i];
+      g.dl[ax][i] = 1.0 / std::sqrt(m);
+    }
+  }
   c->L = g.L;
   c->ws_bytes = plan(c, nullptr);
   *out = c;
@@ -403,25 +411,52 @@ invdft_status invdft_reset(invdft_handle h) {
   return INVDFT_OK;
 }
 
-invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out12) {
+invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16) {
   if (!h) return INVDFT_EINVAL;
   HxProf &p = h->prof;
   if (!cuda_ok(h, prof_flush(h), "profile flush")) return INVDFT_ECUDA;
-  if (out12) {
-    for (int t = 0; t < 3; ++t) {
-      out12[4 * t + 0] = p.ms[t];
-      out12[4 * t + 1] = p.bytes_sum[t];
-      out12[4 * t + 2] = p.flops_sum[t];
-      out12[4 * t + 3] = (double)p.n[t];
+  if (out16) {
+    for (int t = 0; t < 4; ++t) {
+      out16[4 * t + 0] = p.ms[t];
+      out16[4 * t + 1] = p.bytes_sum[t];
+      out16[4 * t + 2] = p.flops_sum[t];
+      out16[4 * t + 3] = (double)p.n[t];
     }
   }
   if (enable) {
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 4; ++t) {
       p.ms[t] = p.bytes_sum[t] = p.flops_sum[t] = 0.0;
       p.n[t] = 0;
     }
   }
   p.on = enable != 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_tune_hx(invdft_handle h, int variant, int seglen, int *nvariants) {
+  if (!h || seglen < 0 || variant < -1) return INVDFT_EINVAL;
+  const int n32 = sweep_variants(h->g, 4), n64 = sweep_variants(h->g, 8);
+  if (variant >= std::max(n32, n64)) {
+    h->err = "tune_hx: variant out of range";
+    return INVDFT_EINVAL;
+  }
+  h->hx_variant_fixed = variant;
+  h->hx_seglen_fixed = seglen;
+  if (nvariants) {
+    nvariants[0] = n32;
+    nvariants[1] = n64;
+  }
+  return INVDFT_OK;
+}
+
+invdft_status invdft_hx_config(invdft_handle h, int ncol, int fp64, int *variant_seglen) {
+  if (!h || !variant_seglen) return INVDFT_EINVAL;
+  const long long key = ((long long)ncol << 8) | ((fp64 ? 8 : 4) << 2);
+  for (int k = 0; k < 4; ++k) {
+    auto it = h->hx_tuned.find(key | k);
+    variant_seglen[2 * k] = it == h->hx_tuned.end() ? -1 : it->second.first;
+    variant_seglen[2 * k + 1] = it == h->hx_tuned.end() ? -1 : it->second.second;
+  }
   return INVDFT_OK;
 }
 

@@ -33,7 +33,9 @@ namespace invdft {
 namespace {
 
 constexpr int kBThreads = 256;
-constexpr long long kWaitLimit = 1LL << 24;   // polls of a phase counter (with back-off)
+// polls of a phase counter (with back-off) before a wait gives up: read from
+// err[1], which the host sets (invdft_batch_set_wait_limit; 2^24 by default,
+// 0 = give up at the first wait)
 
 // column-quad arithmetic on packed FP32 pairs (each lane the IEEE
 // round-to-nearest operation, as in the scalar forms)
@@ -250,6 +252,7 @@ batch_filter_kernel(const BatchProb *__restrict__ probs, int nprob, int m, int p
   __shared__ Shared sh;
   const int tid = threadIdx.x;
   const int total = (m - 1) * per_phase;
+  const long long wait_limit = (long long)ld_acquire((const unsigned *)err + 1);
   if (tid == 0) sh.abort = 0;
   for (;;) {
     __syncthreads();
@@ -269,8 +272,10 @@ batch_filter_kernel(const BatchProb *__restrict__ probs, int nprob, int m, int p
       const unsigned need = (unsigned)bp.items;
       const unsigned *cnt = done + (size_t)b * (m + 1) + (k - 1);
       long long polls = 0;
-      while (ld_acquire(cnt) < need) {
-        if (++polls > kWaitLimit || ld_acquire((const unsigned *)err) != 0) {
+      for (;;) {
+        // a zero limit gives up at the first wait, complete or not
+        if (wait_limit > 0 && ld_acquire(cnt) >= need) break;
+        if (++polls > wait_limit || ld_acquire((const unsigned *)err) != 0) {
           sh.abort = 1;
           break;
         }

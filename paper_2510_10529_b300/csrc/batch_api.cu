@@ -64,6 +64,10 @@ struct BatchState {
 
 namespace {
 
+// Default polls of a phase counter before a wait of the persistent kernel
+// gives up (each poll backs off 256 ns, so well over a second)
+constexpr int kBatchWaitLimit = 1 << 24;
+
 // How long a posted filter waits for the other problems of the batch
 constexpr long long kFilterWindowUs = 500;
 constexpr size_t kMaxGraphs = 64;   // cached launch graphs (sets of problems)
@@ -367,7 +371,12 @@ invdft_status invdft_batch_create(const invdft_handle *handles, int n, invdft_ba
   ok &= cudaMalloc((void **)&B->d_done,
                    (size_t)kMaxBatch * (kMaxBatchDeg + 1) * sizeof(unsigned)) == cudaSuccess;
   ok &= cudaMalloc((void **)&B->d_queue, sizeof(int)) == cudaSuccess;
-  ok &= cudaMalloc((void **)&B->d_err, sizeof(int)) == cudaSuccess;
+  // d_err[0]: error word of the persistent kernel; d_err[1]: its wait limit
+  ok &= cudaMalloc((void **)&B->d_err, 2 * sizeof(int)) == cudaSuccess;
+  if (ok) {
+    const int limit[2] = {0, kBatchWaitLimit};
+    ok &= cudaMemcpy(B->d_err, limit, sizeof(limit), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
   int per_sm = 0, nsm = 0;
   ok &= batch_filter_occupancy(&per_sm) == cudaSuccess;
   ok &= cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) == cudaSuccess;
@@ -457,6 +466,17 @@ invdft_status invdft_batch_step(invdft_batch B, const double *const *rho_data,
     if (st[b] != INVDFT_OK && (worst == INVDFT_OK || worst == INVDFT_ENOCONV)) worst = st[b];
   }
   return worst;
+}
+
+invdft_status invdft_batch_set_wait_limit(invdft_batch B, int polls) {
+  if (!B) return INVDFT_EINVAL;
+  const int limit = polls >= 0 ? polls : kBatchWaitLimit;
+  // the previous step has finished (batch steps are synchronous on the host)
+  if (cudaMemcpy(B->d_err + 1, &limit, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    B->err = "batch_set_wait_limit: copy failed";
+    return INVDFT_ECUDA;
+  }
+  return INVDFT_OK;
 }
 
 invdft_status invdft_batch_info(invdft_batch B, int *chunk_cols, double *info4) {

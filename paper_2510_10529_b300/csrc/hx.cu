@@ -10,6 +10,8 @@
 // exact dense 125x125 (Q4) matrix; applying it as seven 1D contractions of the
 // (p+1)^3 cell tensor gives the same product with 3.5x fewer FP64 operations,
 // which matters because FP64 is the scarce pipe on this part.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace invdft {
@@ -292,18 +294,80 @@ bool uses_tc(const Ctx *c, const HxArgs<float> &a) {
   return a.tc && c->g.p == 4 && c->Ke_tc && a.Z != a.X && a.Z != a.W &&
          (const void *)a.Z != (const void *)a.E;
 }
+template <typename T>
+bool uses_sweep(const Ctx *c, const HxArgs<T> &a) {
+  return sweep_supported(c->g, a.ncol, sizeof(T), a.X, a.Z, a.W, a.E);
+}
+
+// Tile variant and z-segment length of the sweep kernel for this launch: the
+// ones fixed by invdft_tune_hx, else the autotuned pair for (precision, ncol,
+// W, E).  The autotuner times every candidate (each tile variant with the
+// whole z range, halves and quarters) on the first such launch of a large
+// mesh, writing into the launch's own output, and keeps the fastest; on small
+// meshes, or while the stream is being captured, the defaults are used
+// (variant 0, the whole z range).
+template <typename T>
+std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStream_t s) {
+  const int nc = c->g.ncell, nvar = sweep_variants(c->g, sizeof(T));
+  const int fv = c->hx_variant_fixed < nvar ? c->hx_variant_fixed : -1;
+  const int fs = c->hx_seglen_fixed > 0 ? std::min(c->hx_seglen_fixed, nc) : 0;
+  if (fv >= 0 && fs > 0) return {fv, fs};
+  const long long key = ((long long)a.ncol << 8) | (sizeof(T) << 2) | (a.W ? 2 : 0) | (a.E ? 1 : 0);
+  auto it = c->hx_tuned.find(key);
+  if (it != c->hx_tuned.end()) {
+    return {fv >= 0 ? fv : it->second.first, fs > 0 ? fs : it->second.second};
+  }
+  const std::pair<int, int> dflt{fv >= 0 ? fv : 0, fs > 0 ? fs : nc};
+  if (c->L < (1LL << 18)) return dflt;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return dflt;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return dflt;
+  }
+  std::pair<int, int> best = dflt;
+  float best_ms = 1e30f;
+  const int segs[3] = {nc, (nc + 1) / 2, (nc + 3) / 4};
+  for (int var = 0; var < nvar; ++var) {
+    if (fv >= 0 && var != fv) continue;
+    for (int k = 0; k < 3; ++k) {
+      const int seg = fs > 0 ? fs : segs[k];
+      if (fs > 0 && k > 0) break;
+      if (k > 0 && segs[k] == segs[k - 1]) continue;
+      int *err = c->status + kStWaitHxSweep;
+      bool ok = launch_hx_sweep(c->g, v, a, err, var, seg, s) == cudaSuccess;
+      ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+      for (int r = 0; r < 2 && ok; ++r) ok = launch_hx_sweep(c->g, v, a, err, var, seg, s) == cudaSuccess;
+      ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = {var, seg};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  c->hx_tuned[key] = best;
+  return best;
+}
+
+template <typename T>
+cudaError_t sweep_op(Ctx *c, const T *v, const HxArgs<T> &a, cudaStream_t s) {
+  const std::pair<int, int> cfg = sweep_config(c, v, a, s);
+  return launch_hx_sweep(c->g, v, a, c->status + kStWaitHxSweep, cfg.first, cfg.second, s);
+}
 
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
+  if (uses_sweep(c, a)) return sweep_op(c, c->v, a, s);
   return launch_hx(c->g, c->v, a, s);
 }
 cudaError_t dispatch_hx(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
-  const bool tc = uses_tc(c, a);
-  if (tc)
+  if (uses_tc(c, a))
     return launch_hx_tc(c->g, c->v, a, c->Ke_tc, c->cell_perm, c->status + kStWaitHxTc, s);
-  const bool simt_q4 = c->g.p == 4 && c->cell_perm && a.ncol % 4 == 0 && a.Z != a.X &&
-                       a.Z != a.W && (const void *)a.Z != (const void *)a.E;
-  if (simt_q4)
-    return launch_hx_simt_q4(c->g, c->vf, a, c->cell_perm, c->status + kStWaitHxSimt, s);
+  if (uses_sweep(c, a)) return sweep_op(c, c->vf, a, s);
   return launch_hx(c->g, c->v, a, s);
 }
 
@@ -328,9 +392,12 @@ cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   }
   const int k = p.used++;
   const double L = (double)c->L, n = a.ncol, sz = sizeof(T);
-  const int kind = sizeof(T) == 8 ? 0 : (uses_tc(c, a) ? 2 : 1);
-  // X read, Z written, v read (FP32 copy on the CUDA-core FP32 path)
-  double bytes = (2.0 * n * sz + (kind == 1 ? 4.0 : 8.0)) * L;
+  // kinds: 0 FP64, 1 FP32 with the filter's W / E terms, 2 other FP32 (the
+  // MINRES operator), 3 TF32 tensor cores
+  const bool tc = uses_tc(c, a);
+  const int kind = sizeof(T) == 8 ? 0 : (tc ? 3 : ((a.W || a.E) ? 1 : 2));
+  // X read, Z written, v read (the FP32 copy on the FP32 CUDA-core paths)
+  double bytes = (2.0 * n * sz + ((sizeof(T) == 4 && !tc) ? 4.0 : 8.0)) * L;
   if (a.W) bytes += n * sz * L;
   if (a.E) bytes += n * 4.0 * L;
   const double ne = (double)c->g.q * c->g.q * c->g.q;

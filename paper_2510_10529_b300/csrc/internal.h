@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -23,7 +24,7 @@ constexpr int kGramBlocks = 296;    // 2 x 148 SMs: partial sums of tall-skinny 
 // Device status words of the kernels with bounded waits (non-zero: a wait gave
 // up; the solvers read them back with their convergence data)
 constexpr int kStWaitHxTc = 8;      // H~X on the tensor cores
-constexpr int kStWaitHxSimt = 9;    // H~X with TMA brick loads
+constexpr int kStWaitHxSweep = 9;    // H~X in the sweep form (TMA plane loads)
 constexpr int kStWaitGram = 10;     // deflation Gram on the tensor cores
 constexpr int kStWaitCount = 3;
 
@@ -36,6 +37,11 @@ struct Geom {
   double kc;
   double A[kMaxQ * kMaxQ];
   double B[kMaxQ * kMaxQ];
+  // per axis (x, y, z): half the cell size s = h/2, and d = m1^-1/2 at the
+  // local nodes of a cell away from the boundary (an interior vertex has
+  // m1 = 2 s w_0, node i in between m1 = s w_i)
+  double s[3];
+  double dl[3][kMaxQ];
   const double *dm1;        // device [Ni + 2]: 1/sqrt(m1) along one axis (0 at the ends)
   const float *dm1f;        // the same table in FP32 (tensor-core path)
 };
@@ -71,9 +77,9 @@ struct HxProf {
   std::vector<int> kind;
   std::vector<double> bytes, flops;
   int used = 0;
-  // kinds: 0 FP64, 1 FP32 on the CUDA cores, 2 TF32 on the tensor cores
-  double ms[3] = {0, 0, 0}, bytes_sum[3] = {0, 0, 0}, flops_sum[3] = {0, 0, 0};
-  long long n[3] = {0, 0, 0};
+  // kinds: 0 FP64, 1 FP32 with W / E terms (filter), 2 other FP32, 3 TF32
+  double ms[4] = {0, 0, 0, 0}, bytes_sum[4] = {0, 0, 0, 0}, flops_sum[4] = {0, 0, 0, 0};
+  long long n[4] = {0, 0, 0, 0};
 };
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) that only ever raises a
@@ -145,6 +151,10 @@ struct Ctx {
   // pinned host mirror for small read-backs
   double *hbuf = nullptr;           // 16 * kMaxCols doubles
   int nsm = 148;                    // SMs of the device (set at bind)
+  // sweep H~X configuration: fixed by invdft_tune_hx (variant >= 0 and / or
+  // seglen > 0), else autotuned per (ncol, precision, W, E) -> (variant, seglen)
+  int hx_variant_fixed = -1, hx_seglen_fixed = 0;
+  std::map<long long, std::pair<int, int>> hx_tuned;
   cudaStream_t aux_stream = nullptr;  // non-blocking stream for captured work (lazy)
   cudaEvent_t aux_event = nullptr;
 };
@@ -225,8 +235,19 @@ size_t tc_cell_matrix_floats();
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
                          const int *perm, int *err, cudaStream_t s);
 void build_cell_order(int nc, std::vector<int> *perm);
-cudaError_t launch_hx_simt_q4(const Geom &g, const float *vf, const HxArgs<float> &a,
-                              const int *perm, int *err, cudaStream_t s);
+// Owner-computes sweep form of H~X (hx_sweep.cu): FP32 and FP64 blocks on
+// orders 2 and 4, ncol * elem a multiple of 16 bytes, 16-byte aligned blocks,
+// Z not aliasing X, W or E.  variant in [0, sweep_variants) selects the tile
+// shape; seglen = z-cells per CTA (the z range is split into segments of that
+// many cells).  err: device word set to 3 if a wait for a TMA plane gave up.
+bool sweep_supported(const Geom &g, int ncol, size_t elem, const void *X, const void *Z,
+                     const void *W, const void *E);
+int sweep_variants(const Geom &g, size_t elem);
+cudaError_t launch_hx_sweep(const Geom &g, const float *v, const HxArgs<float> &a, int *err,
+                            int variant, int seglen, cudaStream_t s);
+cudaError_t launch_hx_sweep(const Geom &g, const double *v, const HxArgs<double> &a, int *err,
+                            int variant, int seglen, cudaStream_t s);
+
 
 // ------------------------------------------------------------ vector kernels (blas.cu)
 // G[i*n2+j] = sum_a A[a*lda+i] B[a*ldb+j] in FP64 (partials then a fixed-order sum).

@@ -72,7 +72,7 @@ invdft_status fetch_many(Ctx *c, std::initializer_list<Piece> pieces, cudaStream
 // A kernel whose bounded wait gave up leaves its status word set; the solvers
 // read the words back with their convergence data.
 invdft_status check_waits(Ctx *c, const int *w) {
-  static const char *const what[kStWaitCount] = {"H~X (tensor cores)", "H~X (TMA bricks)",
+  static const char *const what[kStWaitCount] = {"H~X (tensor cores)", "H~X (sweep form)",
                                                  "deflation Gram"};
   for (int i = 0; i < kStWaitCount; ++i)
     if (w[i]) {

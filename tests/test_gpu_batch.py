@@ -101,3 +101,33 @@ def test_batch_matches_problems_stepped_alone(cases):
         assert diff <= 1e-7, (b, diff)
         assert abs(st["loss"] - stats_b[b]["loss"]) <= 1e-7 * st["loss"]
     batch.close()
+
+
+def test_batch_phase_wait_timeout_is_reported(cases):
+    """The timeout path of the persistent filter kernel's bounded phase waits,
+    without any device fault: with the wait limit at zero, the first wait of a
+    CTA for the previous phase of a problem gives up at once, the kernel sets
+    its error word and every CTA leaves; the step must return INVDFT_ETIMEOUT.
+    With the default limit restored, the same batch steps normally again (the
+    context and the handles stay usable)."""
+    import paper_2510_10529_b300 as P
+    from paper_2510_10529_b300._lib import INVDFT_ETIMEOUT
+    problems = [_gpu_problem(c, d[1]) for c, d in zip(CASES, cases)]
+    batch = P.Batch(problems)
+    v_xc = [_cuda(np.zeros(d[0].L)) for d in cases]
+    rd = [_cuda(d[2]) for d in cases]
+    w = [_cuda(np.ones(d[0].L)) for d in cases]
+    batch.step(rd, w, v_xc)                      # first step: autotuning, normal waits
+    batch.set_wait_limit(0)
+    with pytest.raises(P.InvdftError) as ei:
+        batch.step(rd, w, v_xc)
+    assert ei.value.status == INVDFT_ETIMEOUT, str(ei.value)
+    assert "timed out" in str(ei.value)
+    batch.set_wait_limit(-1)
+    v_xc = [_cuda(np.zeros(d[0].L)) for d in cases]
+    for p in problems:
+        p.reset()
+    stats, status = batch.step(rd, w, v_xc)
+    assert all(s == 0 for s in status), status
+    assert all(np.isfinite(st["loss"]) for st in stats)
+    batch.close()

@@ -291,3 +291,51 @@ def test_profile_hx_counts_each_kernel_kind():
     # FP32 on the CUDA cores reads the FP32 copy of v: 4 bytes per node
     assert prof["fp32"]["bytes"] == (2 * 12 * 4 + 4) * L
     assert prof["tf32"]["bytes"] == 2 * (2 * 12 * 4 + 8) * L
+
+
+@pytest.fixture(scope="module")
+def bench_shape():
+    """The benchmark workload's shape on a mesh the oracle solves in seconds:
+    the 100-electron, 12-nucleus system of the 32^3-cell benchmark (positions
+    scaled into a [-8, 8]^3 box of 6^3 Q4 cells), 60 states at kT > 0, so that
+    about 50 occupied states enter one adjoint MINRES block and its deflation
+    Gram runs on the tensor cores at that width."""
+    wl = W.cube32_q4_e100()
+    mesh = fe.Mesh(-8.0, 8.0, 6, 4)
+    xyz = mesh.coords()
+    R = wl.nuclei_R * (8.0 / 14.0)
+    rho_m = W.gaussian_density(xyz, R, wl.nuclei_Z, W.MODEL_WIDTH)
+    v_fixed = (W.smeared_coulomb(xyz, R, wl.nuclei_Z, wl.smear)
+               + W.gaussian_density_hartree(xyz, R, wl.nuclei_Z, W.MODEL_WIDTH))
+    v_star = W.lda_exchange(rho_m)
+    rho_d = ks.forward(mesh, v_fixed + v_star, wl.n_electrons, wl.nstates, wl.kT)["rho"]
+    op = inverse.Problem(mesh=mesh, v_fixed=v_fixed, rho_data=rho_d, w=np.ones(mesh.L),
+                         n_electrons=wl.n_electrons, nstates=wl.nstates, kT=wl.kT)
+    v_xc = 0.5 * v_star
+    return wl, mesh, v_fixed, rho_d, v_xc, inverse.evaluate(op, v_xc)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_bench_shape_forward_and_adjoint_match_oracle(bench_shape, prec):
+    wl, mesh, v_fixed, rho_d, v_xc, (L_ora, e_ora, g_ora, fw_ora) = bench_shape
+    pb = _problem(-8.0, 8.0, 6, 4, nstates=wl.nstates, n_electrons=wl.n_electrons, kT=wl.kT,
+                  prec=prec, eig_tol=1e-10, adj_tol=1e-11, cheb_degree=wl.cheb_degree)
+    pb.set_potential(_cuda(v_fixed), _cuda(v_xc))
+    out = pb.forward_solve()
+    occ = out["occ"].cpu().numpy()
+    act = fw_ora["f"] > 1e-8
+    n_adj = int(np.sum(occ > 1e-8))
+    assert n_adj >= 50, n_adj
+    deps = np.abs(out["eps"].cpu().numpy()[act] - fw_ora["eps"][act]).max()
+    m = mesh.mass()
+    drho = math.sqrt(np.sum(m * (out["rho"].cpu().numpy() - fw_ora["rho"]) ** 2))
+    loss, g, st = pb.loss_grad(_cuda(rho_d), _cuda(np.ones(mesh.L)))
+    g = g.cpu().numpy()
+    gerr = np.linalg.norm(g - g_ora) / np.linalg.norm(g_ora)
+    print(f"bench shape ({prec}): {n_adj} adjoint columns, max |d eps| {deps:.2e}, "
+          f"density L2 {drho:.2e}, loss rel {abs(loss - L_ora) / L_ora:.2e}, grad rel {gerr:.2e}, "
+          f"minres iters {st['minres_iters_max']}")
+    assert deps <= 1e-6
+    assert drho <= 1e-6
+    assert abs(loss - L_ora) <= 1e-8 * L_ora
+    assert gerr <= 1e-5
