@@ -1,7 +1,7 @@
 """Benchmark: inverse-DFT iterations per second on one B300 (and replicas).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload cube32_q4_e100] [--prec mixed|fp64]
+                    [--workload cube32_q4_e100] [--prec mixed|fp64] [--fp64-steps K64]
 
 A step is one full inverse iteration through the C ABI (invdft_step): the
 L-BFGS direction, a backtracking line search (one Kohn-Sham solve by
@@ -14,16 +14,31 @@ generated at set-up by a Kohn-Sham solve at a known reference potential (the
 paper's molecular densities are not available).  Every orbital block is
 larger than L2 (0.98 GB in FP64), so no flush is needed between steps.
 
-The JSON line also carries the operator benchmark of the same mesh
-(H~X on 64 vectors, nominal 2 (p+1)^6 N_v n_cells flops), the roofline of the
-dominant kernel (H~X, timed with CUDA events inside the timed steps), the
-oracle as a CPU baseline, an end-to-end figure through host buffers and the
-SM clocks sampled during the timed region.
+Timed steps: each of the K timed steps copies v_xc in from pinned host memory,
+runs invdft_step and copies v_xc and the loss back.  `value` is the device
+time of the steps alone (CUDA events around each invdft_step call on its
+stream); `e2e` is the host wall time of the same steps including both copies.
+
+Headline comparison (the metric's "mixed vs FP64 GPU path at equal
+accuracy"): after the mixed arm, the plain FP64 GPU path runs the same
+trajectory from the same start for K64 steps (1 untimed + K64 - 1 timed by
+default, fewer than the mixed arm because an FP64 step takes tens of
+seconds); the line reports both iteration rates, the e_L2 of both arms after
+every common step, and the relative difference of the two paths' gradients
+at the FP64 arm's last iterate.
+
+The JSON line also carries the operator benchmark of the same mesh (H~X on 64
+vectors in FP32, TF32 and FP64, nominal 2 (p+1)^6 N_v n_cells flops), the
+roofline of the in-step FP32 H~X of the MINRES iterations (CUDA events on its
+stream, algorithmic bytes over device time), the in-step filter launches, the
+oracle as a CPU baseline and the SM clocks sampled during the timed region.
 
 Multi-GPU: the path runs as independent replicas (one problem per rank, no
 collective in the data path); value = steps of all ranks / max rank time.
---impl reference times the FP64 CPU oracle on bounded samples of the same
-workload (rank 0 only).
+--impl reference times the FP64 CPU oracle (rank 0 only): each step is one
+full oracle iteration of the 8^3-cell Q2 two-electron workload (the large
+workload's oracle iteration takes hours; its oracle H~X per column is
+measured and reported, its iteration rate is not run).
 """
 from __future__ import annotations
 
@@ -47,24 +62,14 @@ import workloads as W  # noqa: E402
 
 METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 
-# DRAM bytes per (node, column) of one FP32 CUDA-core H~X launch: ncu
-# dram__bytes_read.sum + dram__bytes_write.sum of hx_simt_kernel<64, 0> (TMA
-# brick version) on the 24^3-cell Q4 mesh (857,375 unknowns) with 60 columns,
-# 486.90 + 190.83 MB, plus the 4-byte zero fill of Z that precedes the kernel
-# in the same launch.  Traffic grows with unknowns x columns, so the in-step
-# figure scales by them.
-HX_SIMT_DRAM_BYTES_PER_NODE_COL = (486.90e6 + 190.83e6) / (857375 * 60) + 4.0
-
-# H~X column-applications per inverse iteration on each workload, as counted by
-# the GPU path (line-search solves, Chebyshev passes, MINRES iterations) over the
-# timed steps of a mixed-precision run (cube32_q4_e100: 32,750 on average over
-# three steps; the smaller workloads carry estimates from their Chebyshev
-# pass and MINRES iteration counts).  The reference arm uses these fixed
-# counts so that it never touches the GPU.
-COL_APPLIES_PER_STEP = {"cube32_q4_e100": 32750,
-                        "cube24_q4_e20": 16 * 31 * 3 + 10 * 200,
-                        "cube8_q2_he": 8 * 21 * 3 + 100, "cube32_q4_hx": 64}
-
+# DRAM bytes per (node, column) of one FP32 sweep-form H~X launch of the MINRES
+# kind (plain epilogue, no W / E): ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of hx_sweep_kernel on the 24^3-cell Q4 mesh (857,375
+# unknowns) with 52 columns, in the tile variant and z-segment length the
+# autotuner picks for the in-step launches (profiles/hx_sweep_cube24_q4_52cols.md).
+# None until that capture exists for the current kernel.
+HX_SWEEP_DRAM_BYTES_PER_NODE_COL = None
+HX_SWEEP_DRAM_SOURCE = "profiles/hx_sweep_cube24_q4_52cols.md"
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -76,11 +81,15 @@ def parse():
                     choices=sorted(W.WORKLOADS) + ["batch16"],
                     help="batch16: the sixteen small problems stepped as one batch")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="steps of the FP64 comparison arm (the first one untimed); 0 skips it")
     ap.add_argument("--no-hx", action="store_true", help="skip the operator benchmark")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ncell", type=int, default=None,
                     help="run the workload on NCELL^3 cells of the same box (a smaller case "
                          "for kernel profiles; the printed line then names that mesh)")
+    ap.add_argument("--oracle-iterations", nargs=2, metavar=("BUDGET_S", "MAX"), default=None,
+                    help=argparse.SUPPRESS)
     ap.add_argument("--hx-case", nargs=3, metavar=("NCELL", "NCOL", "KIND"), default=None,
                     help="only apply H~X three times on an NCELL^3 Q4 mesh with NCOL random "
                          "columns, KIND tf32|fp32|fp64 (a small case for kernel profiles)")
@@ -175,7 +184,10 @@ def build_problem(wl, prec, device):
 
 
 def hx_benchmark(device, reps32=20, reps64=3):
-    """H~X on the 32^3-cell Q4 operator benchmark (64 unit-norm random vectors)."""
+    """H~X on the 32^3-cell Q4 operator benchmark (64 unit-norm random vectors):
+    TF32 tensor cores (dense cell GEMM), FP32 and FP64 sweep form (CUDA cores).
+    Each timing is the mean over `reps` back-to-back launches after warm-up;
+    the blocks (0.5 GB FP32, 1.05 GB FP64) are larger than L2."""
     import torch
 
     import paper_2510_10529_b300 as P
@@ -188,7 +200,9 @@ def hx_benchmark(device, reps32=20, reps64=3):
     out = {}
     ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
     flops = 2.0 * ne * ne * 64 * cells
-    for name, X, reps, tc in (("mixed", X64.float(), reps32, True),
+    pk = peaks()
+    hbm = pk["hbm_gbs"] if pk else 6400.0
+    for name, X, reps, tc in (("tf32", X64.float(), reps32, True),
                               ("fp32", X64.float(), reps32, False), ("fp64", X64, reps64, False)):
         Y = torch.empty_like(X)
         for _ in range(3):
@@ -202,10 +216,16 @@ def hx_benchmark(device, reps32=20, reps64=3):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        byt = (2 * 64 * X.element_size() + 8) * pb.L
-        out[name] = {"ms": ms, "tflops_nominal": flops / ms / 1e9, "gbs": byt / ms / 1e6}
+        # X read, Y written, v read (FP32 copy on the FP32 CUDA-core path)
+        vbytes = 4 if name == "fp32" else 8
+        byt = (2 * 64 * X.element_size() + vbytes) * pb.L
+        out[name] = {"ms": ms, "tflops_nominal": flops / ms / 1e9, "gbs": byt / ms / 1e6,
+                     "hbm_frac": byt / ms / 1e6 / hbm, "algorithmic_bytes": byt}
+        if name != "tf32":
+            out[name]["tuned_variant_seglen"] = pb.hx_config(64, name == "fp64")["plain"]
     pb.close()
-    return {"workload": "cube32_q4_hx", "ncol": 64, "nominal_flops": flops, **out}
+    return {"workload": "cube32_q4_hx", "ncol": 64, "nominal_flops": flops,
+            "peak_gbs": hbm, "peak_source": "measured" if pk else "fallback", **out}
 
 
 def hx_case(ncell, ncol, kind, device):
@@ -232,15 +252,56 @@ def hx_case(ncell, ncol, kind, device):
 
 # ------------------------------------------------------------------ oracle baseline
 
-def oracle_baseline(wl, col_applies_per_step: float, budget_s: float = 12.0):
-    """Time the oracle's H~X (numpy FP64 cell loop) on the full mesh with a few
-    columns, and scale to the column-applications of one GPU step."""
-    from oracle import fe
+def _cores():
     try:
-        from threadpoolctl import threadpool_info
-        cores = max([t.get("num_threads", 1) for t in threadpool_info()] or [1])
-    except Exception:
-        cores = 1
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_iterations_here(budget_s: float, max_iters: int):
+    """Full oracle iterations (oracle.inverse.step: line search with a Kohn-Sham
+    solve per trial, loss, adjoint and gradient) of the 8^3-cell Q2
+    two-electron workload from v_xc = 0, in this process.  The target density
+    (oracle SCF) is set up outside the timing.  Returns (iterations, seconds)."""
+    from oracle import fe, inverse, scf
+    wl = W.cube8_q2_he()
+    mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
+    d = scf.target_density(mesh, wl)
+    op = inverse.Problem(mesh=mesh, v_fixed=d["v_fixed"], rho_data=d["rho_data"],
+                         w=np.ones(mesh.L), n_electrons=wl.n_electrons, nstates=wl.nstates,
+                         kT=wl.kT)
+    st = inverse.State(v_xc=np.zeros(mesh.L))
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_iters:
+        st = inverse.step(op, st)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return n, time.perf_counter() - t0
+
+
+def oracle_iterations(threads: int, budget_s: float, max_iters: int):
+    """_oracle_iterations_here in a child process whose BLAS / OpenMP pools are
+    limited to `threads` (set before numpy loads).  Returns (iterations,
+    seconds, threads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-iterations",
+                        str(budget_s), str(max_iters)], env=env, capture_output=True, text=True,
+                       check=True)
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["iterations"], out["seconds"], threads
+
+
+def oracle_hx_per_column(wl, budget_s: float = 6.0):
+    """Seconds per column of the oracle's H~X (numpy FP64 cell loop) on the
+    workload's full mesh, 2 columns at a time."""
+    from oracle import fe
     mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
     ncol = 2
     X = W.random_block(mesh.L, ncol, wl.seed)
@@ -250,16 +311,56 @@ def oracle_baseline(wl, col_applies_per_step: float, budget_s: float = 12.0):
     while True:
         mesh.apply_Htilde(v, X)
         reps += 1
-        if time.perf_counter() - t0 > budget_s or reps >= 8:
+        if time.perf_counter() - t0 > budget_s or reps >= 4:
             break
-    per_col = (time.perf_counter() - t0) / (reps * ncol)
-    step_s = per_col * col_applies_per_step
-    return {"value": 1.0 / step_s, "unit": "iter/s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle H~X (numpy FP64 cell loop, {wl.name} mesh, {ncol} columns, "
-                       f"{reps} applications, {per_col:.3f} s per column) x "
-                       f"{col_applies_per_step:.0f} column-applications per step; a lower "
-                       "bound on the oracle's time per iteration (its Gram, eigensolver and "
-                       "MINRES vector work are not counted)")}
+    return (time.perf_counter() - t0) / (reps * ncol)
+
+
+def cpu_baseline(wl, budget_s: float = 8.0):
+    """The oracle on the machine's host cores: full iterations of the small
+    workload on one core and on all cores, and the oracle H~X of the bench
+    workload's mesh; no extrapolation to the bench workload's iteration rate
+    (an oracle iteration there takes hours, so it is not run)."""
+    n1, s1, _ = oracle_iterations(1, budget_s, 10)
+    cores = _cores()
+    na, sa, _ = oracle_iterations(cores, budget_s, 10)
+    hx_col = oracle_hx_per_column(wl) if wl.name != "cube8_q2_he" else None
+    return {"value": na / sa, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": (f"full oracle iterations of cube8_q2_he (8^3 Q2 cells, 3,375 unknowns, "
+                       f"2 electrons) from v_xc = 0: {na} in {sa:.2f} s on {cores} cores, "
+                       f"{n1} in {s1:.2f} s on 1 core; the bench workload's oracle iteration "
+                       "is not run (hours); its oracle H~X is timed per column"),
+            "workload": "cube8_q2_he",
+            "one_core": {"value": n1 / s1, "unit": "iter/s", "iterations": n1, "seconds": s1},
+            "all_cores": {"value": na / sa, "unit": "iter/s", "iterations": na, "seconds": sa,
+                          "cores": cores},
+            "bench_workload_oracle_hx": (None if hx_col is None else
+                                         {"workload": wl.name, "seconds_per_column": hx_col,
+                                          "iteration": "not run"})}
+
+
+def small_workload_gpu(device, steps=10, warmup=3):
+    """GPU iterations/s of the mixed path on the cpu_baseline's small workload
+    (the same config as the oracle's timed iterations)."""
+    import torch
+    wl = W.cube8_q2_he()
+    pb, d = build_problem(wl, "mixed", device)
+    v = torch.zeros(pb.L, dtype=torch.float64, device=device)
+    for _ in range(warmup):
+        pb.step(d["rho_data"], d["w"], v)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        pb.step(d["rho_data"], d["w"], v)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pb.close()
+    return {"workload": wl.name, "value": 1e3 / ms, "unit": "iter/s", "steps": steps,
+            "warmup": warmup, "prec": "mixed"}
 
 
 # ------------------------------------------------------------------ arms
@@ -287,6 +388,56 @@ def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> flo
     return world * units_per_rank / seconds_max
 
 
+def fp64_arm(wl, d, device, steps, mixed_traj):
+    """The plain FP64 GPU path on the same workload, from the same start, for
+    `steps` steps (the first untimed); equal accuracy: e_L2 of both arms after
+    every common step, and the two paths' gradients at the FP64 arm's last
+    iterate."""
+    import torch
+
+    import paper_2510_10529_b300 as P
+    pb = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, wl.nstates, n_electrons=wl.n_electrons,
+                   kT=wl.kT, prec="fp64", cheb_degree=wl.cheb_degree, seed=wl.seed + 1,
+                   device=device)
+    pb.set_potential(d["v_fixed"], None)
+    v = torch.zeros(pb.L, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream()
+    traj, ms = [], []
+    for k in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = pb.step(d["rho_data"], d["w"], v)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        traj.append(st["err_l2"])
+        if k >= 1:
+            ms.append(e0.elapsed_time(e1))
+    common = min(len(traj), len(mixed_traj))
+    rel = [abs(a - b) / b for a, b in zip(mixed_traj[:common], traj[:common])]
+    pb.close()
+    # both paths' gradients at the same potential (the FP64 arm's last
+    # iterate), from fresh handles with the same fixed tight tolerances (the
+    # adaptive ones depend on each handle's last e_L2)
+    grads = {}
+    for prec in ("fp64", "mixed"):
+        q = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, wl.nstates, n_electrons=wl.n_electrons,
+                      kT=wl.kT, prec=prec, cheb_degree=wl.cheb_degree, seed=wl.seed + 1,
+                      eig_tol=1e-9, adj_tol=1e-10, device=device)
+        q.set_potential(d["v_fixed"], v)
+        _, g, _ = q.loss_grad(d["rho_data"], d["w"])
+        grads[prec] = g
+        q.close()
+    grad_rel = ((grads["mixed"] - grads["fp64"]).norm() / grads["fp64"].norm()).item()
+    out = {"value": (1e3 / statistics.mean(ms)) if ms else None, "unit": "iter/s",
+           "steps_timed": len(ms), "untimed": 1, "ms_per_step": statistics.mean(ms) if ms else None,
+           "err_l2": traj, "err_l2_mixed_same_steps": list(mixed_traj[:common]),
+           "err_l2_rel_diff_max": max(rel) if rel else None,
+           "grad_rel_diff_at_fp64_iterate": grad_rel,
+           "grad_tolerances": {"eig_tol": 1e-9, "adj_tol": 1e-10}}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -301,8 +452,9 @@ def run_ours(args, rank, world):
     pb, d = build_problem(wl, args.prec, device)
     v_xc = torch.zeros(pb.L, dtype=torch.float64, device=device)
     rd, w = d["rho_data"], d["w"]
+    traj = []
     for _ in range(args.warmup):
-        pb.step(rd, w, v_xc)
+        traj.append(pb.step(rd, w, v_xc)["err_l2"])
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -311,75 +463,95 @@ def run_ours(args, rank, world):
     pb.profile_hx(True)
     launches0 = P.invdft_kernel_launches()
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # timed steps: v_xc in from pinned host memory, the step, v_xc back out;
+    # device time of the step alone (value) and wall time with the copies (e2e)
+    v_host = v_xc.cpu().pin_memory()
     torch.cuda.synchronize()
-    # INVDFT_PROFILE_TIMED=1 brackets the timed steps for a profiler started
-    # with capture off (ncu --profile-from-start off); it changes no work
-    profile_timed = os.environ.get("INVDFT_PROFILE_TIMED") == "1"
-    if profile_timed:
-        torch.cuda.profiler.start()
-    e0.record(stream)
-    stats = []
+    dev_ms, wall_s, stats = 0.0, 0.0, []
     for _ in range(args.steps):
-        stats.append(pb.step(rd, w, v_xc))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if profile_timed:
-        torch.cuda.profiler.stop()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        v_xc.copy_(v_host, non_blocking=True)
+        e0.record(stream)
+        st = pb.step(rd, w, v_xc)
+        e1.record(stream)
+        v_host.copy_(v_xc, non_blocking=True)
+        torch.cuda.synchronize()
+        wall_s += time.perf_counter() - t0
+        dev_ms += e0.elapsed_time(e1)
+        stats.append(st)
+        traj.append(st["err_l2"])
     launches = P.invdft_kernel_launches() - launches0
     prof = pb.profile_hx(False)
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = dev_ms / args.steps
     ms_max = max_over_ranks(ms, world, device)
+    e2e_s = max_over_ranks(wall_s / args.steps, world, device)
+    value = whole_job_rate(1.0, world, ms_max / 1e3)
+    e2e = {"value": whole_job_rate(1.0, world, e2e_s), "unit": "iter/s",
+           "h2d_bytes_per_step": pb.L * 8, "d2h_bytes_per_step": pb.L * 8 + 8,
+           "steps": "the timed steps (same as value)"}
     if world > 1:
         dist.barrier()
-    value = whole_job_rate(1.0, world, ms_max / 1e3)
-
-    # end to end through host buffers: v_xc pinned on the host, copied in and
-    # out every step, plus the loss read back
-    v_host = v_xc.cpu().pin_memory()
-    e2e_steps = max(1, min(args.steps, 2))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        v_dev = v_host.to(device, non_blocking=True)
-        pb.step(rd, w, v_dev)
-        v_host.copy_(v_dev, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, device)
-    e2e = {"value": whole_job_rate(1.0, world, e2e_s), "unit": "iter/s",
-           "h2d_bytes_per_step": pb.L * 8, "d2h_bytes_per_step": pb.L * 8 + 8}
-
     if rank != 0:
         if world > 1:
-            dist.barrier()
             dist.destroy_process_group()
         return
-    hx = None if args.no_hx else hx_benchmark(device)
     pk = peaks()
-    simt = prof["fp32"]["launches"] > 0
-    k32 = prof["fp32"] if simt else prof["fp64"]
-    nl = max(1, k32["launches"])
-    achieved = k32["bytes"] / (k32["ms"] * 1e6) if k32["ms"] > 0 else None
     peak_gbs = pk["hbm_gbs"] if pk else 6400.0
     ne, cells = (wl.order + 1) ** 3, wl.ncell ** 3
-    col_applies = sum(prof[k]["flops"] for k in ("fp64", "fp32", "tf32")) / (2.0 * ne * ne * cells)
-    bytes_per_launch = k32["bytes"] / nl
+
+    def kind_summary(k, label):
+        r = prof[k]
+        nl = int(r["launches"])
+        if nl == 0:
+            return None
+        cols = r["flops"] / (2.0 * ne * ne * cells) / nl     # columns per launch (exact)
+        ach = r["bytes"] / (r["ms"] * 1e6)
+        out = {"kernel": label, "launches": nl, "avg_launch_ms": r["ms"] / nl,
+               "columns_per_launch": cols, "algorithmic_bytes_per_launch": r["bytes"] / nl,
+               "achieved_gbs": ach, "hbm_frac": ach / peak_gbs,
+               "ms_per_step": r["ms"] / args.steps}
+        if k != "tf32" and abs(cols - round(cols)) < 1e-9:
+            out["tuned_variant_seglen"] = pb.hx_config(int(round(cols)), k == "fp64")
+        return out
+
+    minres_kind = "fp32" if args.prec == "mixed" else "fp64"
+    km = kind_summary(minres_kind, "hx_sweep_kernel: H~X of the MINRES iterations and the "
+                      "other plain launches (" + ("FP32" if args.prec == "mixed" else "FP64")
+                      + " sweep form, CUDA cores)")
+    kf = kind_summary("fp32_filter", "hx_sweep_kernel: FP32 H~X of the defect-corrected "
+                      "Chebyshev filter (W and E terms, CUDA cores)")
+    kt = kind_summary("tf32", "hx_tc_kernel: TF32 H~X of the Chebyshev filter (tensor cores)")
     traffic = None
-    if simt:
-        ncol_avg = (bytes_per_launch / pb.L - 4.0) / 8.0
-        traffic = HX_SIMT_DRAM_BYTES_PER_NODE_COL * pb.L * ncol_avg
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-            "frac": (achieved / peak_gbs) if achieved else None, "traffic": traffic,
-            "kernel": ("hx_simt_kernel: FP32 H~X of the MINRES iterations (CUDA cores)" if simt
-                       else "hx_cells + hx_nodal: FP64 H~X"),
-            "launches": int(k32["launches"]), "avg_launch_ms": k32["ms"] / nl,
-            "peak_source": "measured" if pk else "fallback",
-            "algorithmic_bytes_per_launch": bytes_per_launch}
+    if km and args.prec == "mixed" and HX_SWEEP_DRAM_BYTES_PER_NODE_COL:
+        traffic = HX_SWEEP_DRAM_BYTES_PER_NODE_COL * pb.L * km["columns_per_launch"]
+    roof = None
+    if km:
+        roof = {"bound": "hbm", "achieved": km["achieved_gbs"], "peak": peak_gbs, "unit": "GB/s",
+                "frac": km["hbm_frac"], "traffic": traffic,
+                "traffic_source": (f"ncu DRAM bytes per (node, column), {HX_SWEEP_DRAM_SOURCE}, "
+                                   "scaled by unknowns x columns of the in-step launches"
+                                   if traffic else "no capture of the current kernel"),
+                "kernel": km["kernel"], "launches": km["launches"],
+                "avg_launch_ms": km["avg_launch_ms"],
+                "columns_per_launch": km["columns_per_launch"],
+                "peak_source": "measured" if pk else "fallback",
+                "algorithmic_bytes_per_launch": km["algorithmic_bytes_per_launch"]}
+    col_applies = sum(prof[k]["flops"] for k in prof) / (2.0 * ne * ne * cells)
+    hx = None if args.no_hx else hx_benchmark(device)
+    fp64 = None
+    if args.prec == "mixed" and args.fp64_steps > 0 and not args.ncell:
+        pb.close()
+        fp64 = fp64_arm(wl, d, device, args.fp64_steps, traj)
+    small = None if args.no_cpu else small_workload_gpu(device)
     cpu = None
     if not args.no_cpu:
-        cpu = oracle_baseline(wl, col_applies / args.steps)
+        try:
+            cpu = cpu_baseline(wl)
+        except Exception as exc:          # the GPU line must not be lost to a host failure
+            cpu = {"value": None, "unit": "iter/s", "kind": "oracle", "error": repr(exc)}
     line = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -391,8 +563,10 @@ def run_ours(args, rank, world):
                    "l2": "inputs larger than L2 (orbital blocks 0.98 GB FP64), no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-        "clocks": clk, "hx": hx,
+        "clocks": clk, "hx": hx, "fp64_gpu": fp64, "small_workload_gpu": small,
+        "hx_in_step": {"minres": km, "filter": kf, "filter_tf32": kt},
         "step_stats": {"loss_last": stats[-1]["loss"], "err_l2_last": stats[-1]["err_l2"],
+                       "err_l2": traj,
                        "cheb_passes": [s["cheb_passes"] for s in stats],
                        "minres_iters": [s["minres_iters_max"] for s in stats],
                        "ls_trials": [s["ls_trials"] for s in stats],
@@ -401,15 +575,10 @@ def run_ours(args, rank, world):
                        "t_forward_ms": [s["t_forward_ms"] for s in stats],
                        "t_adjoint_ms": [s["t_adjoint_ms"] for s in stats],
                        "col_applies_per_step": col_applies / args.steps,
-                       "hx_ms_share": sum(prof[k]["ms"] for k in ("fp64", "fp32", "tf32"))
-                       / (ms_max * args.steps),
-                       "hx_fp64_ms_per_step": prof["fp64"]["ms"] / args.steps,
-                       "hx_fp32_ms_per_step": prof["fp32"]["ms"] / args.steps,
-                       "hx_tf32_ms_per_step": prof["tf32"]["ms"] / args.steps},
+                       "hx_ms_share": sum(prof[k]["ms"] for k in prof) / (ms_max * args.steps)},
     }
     print(json.dumps(line), flush=True)
     if world > 1:
-        dist.barrier()
         dist.destroy_process_group()
 
 
@@ -503,29 +672,47 @@ def run_batch(args, rank, world):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores: each step is one full oracle
+    iteration of the 8^3-cell Q2 two-electron workload (all cores), after W
+    untimed ones; the bench workload's oracle H~X per column is measured and
+    reported beside it (its iteration is not run: hours)."""
     if rank != 0:
         return
     wl = W.WORKLOADS[args.workload]()
-    per_step = COL_APPLIES_PER_STEP[wl.name]
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(oracle_baseline(wl, per_step, budget_s=4.0))
-    vals = vals[args.warmup:]
-    v = statistics.median([x["value"] for x in vals])
+    small = W.cube8_q2_he()
+    cores = _cores()
+    n_w, s_w, _ = oracle_iterations(cores, 1e9, args.warmup) if args.warmup else (0, 0.0, cores)
+    n, sec, _ = oracle_iterations(cores, 1e9, args.steps)
+    v = n / sec
+    hx_col = oracle_hx_per_column(wl) if wl.name != small.name else None
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "cells": f"{wl.ncell}^3", "order": wl.order,
-                       "unknowns": wl.n_interior, "nstates": wl.nstates,
-                       "n_electrons": wl.n_electrons, "parallelism": "cpu"},
-            "cpu_baseline": {**vals[-1], "value": v},
+            "config": {"workload": small.name, "cells": f"{small.ncell}^3", "order": small.order,
+                       "unknowns": small.n_interior, "nstates": small.nstates,
+                       "n_electrons": small.n_electrons, "parallelism": "cpu",
+                       "note": (f"the oracle iteration of {wl.name} takes hours and is not run; "
+                                "this arm times full oracle iterations of the small workload "
+                                "(the GPU arm reports its own rate on it as "
+                                "small_workload_gpu)")},
+            "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} full oracle iterations of {small.name} "
+                                       f"(after {n_w} untimed), {sec:.2f} s, {cores} cores"},
+            "bench_workload_oracle_hx": (None if hx_col is None else
+                                         {"workload": wl.name, "seconds_per_column": hx_col,
+                                          "iteration": "not run"}),
             "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.oracle_iterations:
+        n, sec = _oracle_iterations_here(float(args.oracle_iterations[0]),
+                                         int(args.oracle_iterations[1]))
+        print(json.dumps({"iterations": n, "seconds": sec}))
+        return
     if args.hx_case:
         n, k, kind = args.hx_case
         if kind not in ("tf32", "fp32", "fp64"):
