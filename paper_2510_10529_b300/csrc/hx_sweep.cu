@@ -50,9 +50,13 @@ namespace {
 
 constexpr long long kSweepSpin = 1LL << 28;   // polls before a TMA wait gives up
 
-template <typename T> struct Vec2;
-template <> struct Vec2<float> { using type = float2; };
-template <> struct Vec2<double> { using type = double2; };
+// The columns a thread carries: VW = 2 (a column pair, packed FP32 or two
+// FP64 lanes) or VW = 1 (one column, scalar arithmetic).
+template <typename T, int VW> struct VecOf;
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<double, 1> { using type = double; };
 
 // column-pair arithmetic: packed FP32 pairs (each lane an IEEE round-to-nearest
 // operation) or two FP64 operations
@@ -62,7 +66,6 @@ __device__ __forceinline__ float2 vfma(float a, float2 x, float2 y) {
 __device__ __forceinline__ double2 vfma(double a, double2 x, double2 y) {
   return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
 }
-__device__ __forceinline__ float2 vmul(float a, float2 x) { return __fmul2_rn(make_float2(a, a), x); }
 __device__ __forceinline__ double2 vmul(double a, double2 x) { return make_double2(a * x.x, a * x.y); }
 __device__ __forceinline__ float2 vadd(float2 x, float2 y) { return __fadd2_rn(x, y); }
 __device__ __forceinline__ double2 vadd(double2 x, double2 y) {
@@ -84,34 +87,71 @@ __device__ __forceinline__ double2 vfmav(double2 a, double2 x, double2 y) {
 // them straight from the parameter space; FP64 ones as scalars
 __device__ __forceinline__ float2 vfma(float2 a, float2 x, float2 y) { return __ffma2_rn(a, x, y); }
 __device__ __forceinline__ float2 vmul(float2 a, float2 x) { return __fmul2_rn(a, x); }
-template <typename T> struct CoefOf;
-template <> struct CoefOf<float> {
+template <typename T, int VW> struct CoefOf;
+template <> struct CoefOf<float, 2> {
   using type = float2;
   static float2 make(double x) { return make_float2((float)x, (float)x); }
 };
-template <> struct CoefOf<double> {
+template <> struct CoefOf<float, 1> {
+  using type = float;
+  static float make(double x) { return (float)x; }
+};
+template <int VW> struct CoefOf<double, VW> {
   using type = double;
   static double make(double x) { return x; }
 };
+// scalar (one column per thread) forms
+__device__ __forceinline__ float vfma(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ __forceinline__ double vfma(double a, double x, double y) { return fma(a, x, y); }
+__device__ __forceinline__ float vmul(float a, float x) { return a * x; }
+__device__ __forceinline__ double vmul(double a, double x) { return a * x; }
+__device__ __forceinline__ float vadd(float x, float y) { return x + y; }
+__device__ __forceinline__ double vadd(double x, double y) { return x + y; }
+__device__ __forceinline__ float vsub(float x, float y) { return x - y; }
+__device__ __forceinline__ double vsub(double x, double y) { return x - y; }
+__device__ __forceinline__ float vfmav(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ __forceinline__ double vfmav(double a, double x, double y) { return fma(a, x, y); }
+// VW consecutive values of a per-column table / block as one V
+template <typename V, typename T> __device__ __forceinline__ V vload(const T *p);
+template <> __device__ __forceinline__ float2 vload<float2, float>(const float *p) {
+  return make_float2(p[0], p[1]);
+}
+template <> __device__ __forceinline__ double2 vload<double2, double>(const double *p) {
+  return make_double2(p[0], p[1]);
+}
+template <> __device__ __forceinline__ float vload<float, float>(const float *p) { return p[0]; }
+template <> __device__ __forceinline__ double vload<double, double>(const double *p) { return p[0]; }
+// s - v per lane
+__device__ __forceinline__ float2 vrsub(float s, float2 v) { return make_float2(s - v.x, s - v.y); }
+__device__ __forceinline__ double2 vrsub(double s, double2 v) { return make_double2(s - v.x, s - v.y); }
+__device__ __forceinline__ float vrsub(float s, float v) { return s - v; }
+__device__ __forceinline__ double vrsub(double s, double v) { return s - v; }
+// the defect block E (FP32) at VW columns
+template <typename V> __device__ __forceinline__ V eload(const float *p);
+template <> __device__ __forceinline__ float2 eload<float2>(const float *p) {
+  return __ldg(reinterpret_cast<const float2 *>(p));
+}
+template <> __device__ __forceinline__ float eload<float>(const float *p) { return __ldg(p); }
 template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ double vzero<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 
 // Coefficients passed by value (kernel parameter space).  x and y: even / odd
 // blocks of the d-scaled centrosymmetric cell blocks (see split / apply);
 // z: the dense d-scaled blocks with alpha / 2 folded in, [i][k].
-template <typename T, int P>
+template <typename CT, int P>
 struct SweepCoef {
-  using CT = typename CoefOf<T>::type;
   static constexpr int H = P / 2, NE = (H + 1) * (H + 1), NO = H * H, Q = P + 1;
   CT eAx[NE], oAx[NO], eBx[NE], oBx[NO];
   CT eAy[NE], oAy[NO], eBy[NE], oBy[NO];
   CT Az[Q * Q], Bz[Q * Q];
 };
 
-template <typename T, int P>
+template <typename T, typename CT, int P>
 struct SweepArgs {
-  SweepCoef<T, P> cf;
+  SweepCoef<CT, P> cf;
   T *Z;
   const T *W;
   const float *E;
@@ -126,10 +166,10 @@ struct SweepArgs {
 };
 
 // tile shape of a variant
-template <typename T, int P, int C, int TX, int TY, int XPT>
+template <typename T, int P, int C, int TX, int TY, int XPT, int VW>
 struct SweepShape {
-  using V = typename Vec2<T>::type;
-  static constexpr int H = P / 2, NCP = C / 2, RX = TX + P + 1, RY = TY + P + 1;
+  using V = typename VecOf<T, VW>::type;
+  static constexpr int H = P / 2, NCP = C / VW, RX = TX + P + 1, RY = TY + P + 1;
   static constexpr int NJX = TX / P, NJY = TY / P, NTH = TX * NJY * NCP;
   // x tasks: XPT consecutive x-cells of one row for one column pair
   static constexpr int NXT = NJX / XPT;
@@ -147,7 +187,7 @@ struct SweepShape {
   static constexpr size_t smem(int nst) {
     return 128 + (size_t)nst * STAGE_STRIDE_V * sizeof(V) + 4 * (size_t)RY * PXS * sizeof(V);
   }
-  static_assert(TX % P == 0 && TY % P == 0 && C % 2 == 0 && (TX / P) % XPT == 0, "tile shape");
+  static_assert(TX % P == 0 && TY % P == 0 && C % VW == 0 && (TX / P) % XPT == 0, "tile shape");
   static_assert((PAD_B % (int)sizeof(V)) == 0, "row padding");
 };
 
@@ -239,12 +279,14 @@ __device__ __forceinline__ V row0(const V *e, const V *o, const CT *eM, const CT
   return acc;
 }
 
-template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, bool HW, bool HE>
-__global__ void __launch_bounds__(SweepShape<T, P, C, TX, TY, XPT>::NTH, MINB)
-hx_sweep_kernel(const __grid_constant__ SweepArgs<T, P> p, const __grid_constant__ CUtensorMap tmx) {
-  using S = SweepShape<T, P, C, TX, TY, XPT>;
+template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
+          bool HE>
+__global__ void __launch_bounds__(SweepShape<T, P, C, TX, TY, XPT, VW>::NTH, MINB)
+hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::type, P> p,
+                const __grid_constant__ CUtensorMap tmx) {
+  using S = SweepShape<T, P, C, TX, TY, XPT, VW>;
   using V = typename S::V;
-  using CT = typename CoefOf<T>::type;
+  using CT = typename CoefOf<T, VW>::type;
   constexpr int H = S::H, NCP = S::NCP, RX = S::RX, RY = S::RY, NTH = S::NTH, PXS = S::PXS;
   constexpr uint32_t kStageBytes = (uint32_t)(S::STAGE_V * sizeof(V));
   static_assert(!HE || std::is_same<T, float>::value, "the defect block is FP32");
@@ -256,7 +298,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, P> p, const __grid_constant
   __shared__ __align__(8) uint64_t full[NST];
   __shared__ T sash[C], sesc[C];
   __shared__ int abort_flag;
-  const SweepCoef<T, P> &cf = p.cf;
+  const SweepCoef<CT, P> &cf = p.cf;
   const int tid = threadIdx.x;
 
   // work item: (tile, column chunk, z segment)
@@ -297,13 +339,9 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, P> p, const __grid_constant
   const int ox = (tid / NCP) % TX;
   const int jy = tid / (NCP * TX);
   const int ux = gx0 + ox;
-  const int colp = c0 + 2 * cv;
+  const int colp = c0 + VW * cv;
   const bool cx_in = ux < p.nx && colp < p.ncol;
-  V ash, esc;
-  ash.x = sash[2 * cv];
-  ash.y = sash[2 * cv + 1];
-  esc.x = sesc[2 * cv];
-  esc.y = sesc[2 * cv + 1];
+  const V ash = vload<V>(sash + VW * cv), esc = vload<V>(sesc + VW * cv);
   const T alpha = (T)p.alpha, beta = (T)p.beta;
   V acc[P + 1][P];
 #pragma unroll
@@ -321,13 +359,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, P> p, const __grid_constant
         const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
         V val = a[yi];
         if (HW) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
-        if (HE) {
-          const float2 e2 = __ldg(reinterpret_cast<const float2 *>(p.E + off));
-          V ev;
-          ev.x = e2.x;
-          ev.y = e2.y;
-          val = vfmav(esc, ev, val);
-        }
+        if constexpr (HE) val = vfmav(esc, eload<V>(p.E + off), val);
         *reinterpret_cast<V *>(p.Z + off) = val;
       }
     }
@@ -438,10 +470,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, P> p, const __grid_constant
     for (int yi = 0; yi < P; ++yi) {
       const int oy = jy * P + yi;
       const V xv = stg[((oy + 1) * RX + ox + 1) * NCP + cv];
-      V a;
-      a.x = alpha * vv[yi] - ash.x;
-      a.y = alpha * vv[yi] - ash.y;
-      nod[yi] = vfmav(a, xv, vzero<V>());
+      nod[yi] = vfmav(vrsub(alpha * vv[yi], ash), xv, vzero<V>());
     }
 
     // ---- z: accumulate the planes of the current z-cell
@@ -547,38 +576,42 @@ void scaled_blocks(const Geom &g, int axis, double *Ah, double *Bh) {
     }
 }
 // even / odd blocks of a centrosymmetric matrix (symmetrised first)
-template <int P, typename T, typename CT>
+template <int P, typename T, int VW, typename CT>
 void eo_blocks(const double *M, CT *e, CT *o) {
   constexpr int H = P / 2, Q = P + 1;
   auto sym = [&](int i, int j) { return 0.5 * (M[i * Q + j] + M[(P - i) * Q + (P - j)]); };
   for (int i = 0; i <= H; ++i)
     for (int k = 0; k <= H; ++k)
-      e[i * (H + 1) + k] = CoefOf<T>::make(k < H ? 0.5 * (sym(i, k) + sym(i, P - k)) : sym(i, H));
+      e[i * (H + 1) + k] =
+          CoefOf<T, VW>::make(k < H ? 0.5 * (sym(i, k) + sym(i, P - k)) : sym(i, H));
   for (int i = 0; i < H; ++i)
-    for (int k = 0; k < H; ++k) o[i * H + k] = CoefOf<T>::make(0.5 * (sym(i, k) - sym(i, P - k)));
+    for (int k = 0; k < H; ++k)
+      o[i * H + k] = CoefOf<T, VW>::make(0.5 * (sym(i, k) - sym(i, P - k)));
 }
 
-template <typename T, int P>
-void make_coef(const Geom &g, double alpha, SweepCoef<T, P> *cf) {
+template <typename T, int VW, int P, typename CT>
+void make_coef(const Geom &g, double alpha, SweepCoef<CT, P> *cf) {
   constexpr int Q = P + 1;
   double Ah[Q * Q], Bh[Q * Q];
   scaled_blocks<P>(g, 0, Ah, Bh);
-  eo_blocks<P, T>(Ah, cf->eAx, cf->oAx);
-  eo_blocks<P, T>(Bh, cf->eBx, cf->oBx);
+  eo_blocks<P, T, VW>(Ah, cf->eAx, cf->oAx);
+  eo_blocks<P, T, VW>(Bh, cf->eBx, cf->oBx);
   scaled_blocks<P>(g, 1, Ah, Bh);
-  eo_blocks<P, T>(Ah, cf->eAy, cf->oAy);
-  eo_blocks<P, T>(Bh, cf->eBy, cf->oBy);
+  eo_blocks<P, T, VW>(Ah, cf->eAy, cf->oAy);
+  eo_blocks<P, T, VW>(Bh, cf->eBy, cf->oBy);
   scaled_blocks<P>(g, 2, Ah, Bh);
   for (int i = 0; i < Q * Q; ++i) {
-    cf->Az[i] = CoefOf<T>::make(0.5 * alpha * Ah[i]);
-    cf->Bz[i] = CoefOf<T>::make(0.5 * alpha * Bh[i]);
+    cf->Az[i] = CoefOf<T, VW>::make(0.5 * alpha * Ah[i]);
+    cf->Bz[i] = CoefOf<T, VW>::make(0.5 * alpha * Bh[i]);
   }
 }
 
-template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, bool HW, bool HE>
-cudaError_t run_sweep(const SweepArgs<T, P> &a, const CUtensorMap &tm, int nitems, cudaStream_t s) {
-  using Sh = SweepShape<T, P, C, TX, TY, XPT>;
-  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, HW, HE>;
+template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
+          bool HE>
+cudaError_t run_sweep(const SweepArgs<T, typename CoefOf<T, VW>::type, P> &a, const CUtensorMap &tm,
+                      int nitems, cudaStream_t s) {
+  using Sh = SweepShape<T, P, C, TX, TY, XPT, VW>;
+  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, VW, HW, HE>;
   const size_t smem = Sh::smem(NST);
   cudaError_t e = raise_smem_limit(k, smem);
   if (e != cudaSuccess) return e;
@@ -589,13 +622,13 @@ cudaError_t run_sweep(const SweepArgs<T, P> &a, const CUtensorMap &tm, int nitem
 
 // One tile variant: C columns per CTA, a TX x TY owned column of nodes, NST
 // planes in flight, XPT x-cells per x task, MINB CTAs per SM for the
-// register budget.
-template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB>
+// register budget, VW columns per thread.
+template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW>
 cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *err, int seglen,
                           cudaStream_t s) {
-  using Sh = SweepShape<T, P, C, TX, TY, XPT>;
-  SweepArgs<T, P> sa;
-  make_coef<T, P>(g, a.alpha, &sa.cf);
+  using Sh = SweepShape<T, P, C, TX, TY, XPT, VW>;
+  SweepArgs<T, typename CoefOf<T, VW>::type, P> sa;
+  make_coef<T, VW>(g, a.alpha, &sa.cf);
   sa.Z = a.Z;
   sa.W = a.W;
   sa.E = a.E;
@@ -635,13 +668,13 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   const bool hw = a.W != nullptr, he = a.E != nullptr;
   const int n = (int)nitems;
   if constexpr (std::is_same<T, float>::value) {
-    if (hw && he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, true, true>(sa, tm, n, s);
-    if (he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, false, true>(sa, tm, n, s);
+    if (hw && he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, true>(sa, tm, n, s);
+    if (he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, true>(sa, tm, n, s);
   } else {
     if (he) return cudaErrorInvalidValue;
   }
-  if (hw) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, true, false>(sa, tm, n, s);
-  return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, false, false>(sa, tm, n, s);
+  if (hw) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, false>(sa, tm, n, s);
+  return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, false>(sa, tm, n, s);
 }
 
 using SweepFn32 = cudaError_t (*)(const Geom &, const float *, const HxArgs<float> &, int *, int,
@@ -650,17 +683,21 @@ using SweepFn64 = cudaError_t (*)(const Geom &, const double *, const HxArgs<dou
                                   int, cudaStream_t);
 // Tile variants per (precision, order), the first one the default.
 const SweepFn32 kVar32q4[] = {
-    sweep_variant<float, 4, 8, 16, 16, 4, 2, 2>,    // 256 threads, two CTAs per SM
-    sweep_variant<float, 4, 16, 16, 16, 3, 1, 1>,   // 512 threads, one x-cell per x task
-    sweep_variant<float, 4, 16, 16, 16, 4, 2, 1>,   // 512 threads, four planes in flight
-    sweep_variant<float, 4, 8, 16, 32, 4, 2, 1>,    // 512 threads, taller tile (less halo)
+    sweep_variant<float, 4, 8, 16, 16, 4, 2, 2, 2>,   // 256 threads, two CTAs per SM
+    sweep_variant<float, 4, 16, 16, 16, 3, 1, 1, 2>,  // 512 threads, one x-cell per x task
+    sweep_variant<float, 4, 16, 16, 16, 4, 2, 1, 2>,  // 512 threads, four planes in flight
+    sweep_variant<float, 4, 8, 16, 32, 4, 2, 1, 2>,   // 512 threads, taller tile (less halo)
 };
-const SweepFn32 kVar32q2[] = {sweep_variant<float, 2, 16, 16, 8, 3, 2, 1>};
+// (one column per thread in FP32 -- scalar FMAs instead of packed pairs -- was
+// measured at 0.81 to 1.18 ms against 0.51 ms on the 32^3 x 64 case, and is not
+// offered)
+const SweepFn32 kVar32q2[] = {sweep_variant<float, 2, 16, 16, 8, 3, 2, 1, 2>};
 const SweepFn64 kVar64q4[] = {
-    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1>,
-    sweep_variant<double, 4, 8, 16, 16, 3, 1, 1>,
+    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 1>,  // one column per thread, 512 threads
+    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 2>,  // column pairs, 256 threads
+    sweep_variant<double, 4, 8, 16, 16, 3, 1, 1, 2>,
 };
-const SweepFn64 kVar64q2[] = {sweep_variant<double, 2, 8, 16, 8, 3, 2, 1>};
+const SweepFn64 kVar64q2[] = {sweep_variant<double, 2, 8, 16, 8, 3, 2, 1, 2>};
 template <typename A, size_t N> constexpr int count_of(const A (&)[N]) { return (int)N; }
 
 }  // namespace
