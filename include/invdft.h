@@ -316,6 +316,41 @@ invdft_status invdft_loss_reduce_noalloc(const double *rho, const double *rho_da
                                          const double *w, const double *mass, long long L,
                                          double *out3, double *dLdrho, void *stream);
 
+/* Initial guess of v_xc (Sec. 4.2.3, Eq. 25-26) at the unknown nodes:
+ *   v_out = f v0[rho] + (1 - f) alpha v_FA,  f = rho / (rho + tau),
+ *   v_FA = -v_H / N_e (Fermi-Amaldi; N_e = opts.n_electrons > 0),
+ *   v0 = v_x + v_c, v_c the PW92 correlation potential (spin-unpolarised),
+ *   v_x the Slater exchange potential (exchange = 0) or the LB94 exchange
+ *   potential of the closed-shell density (exchange = 1), with rho = max(
+ *   rho_data, 0) and |grad rho| from the finite-element interpolant of rho at
+ *   the GLL nodes (at a cell vertex the mean of the two cells' one-sided
+ *   derivatives; rho = 0 on the Dirichlet boundary).
+ * rho_data, v_H (the Hartree potential of rho_data, the same one that enters
+ * v_fixed), v_out: device [L].  tau > 0 (the paper suggests 1e-2); alpha
+ * scales the Fermi-Amaldi tail (1 gives -1/r far out).  The LB94 form uses a
+ * work vector of the bound workspace: do not run it concurrently with a step
+ * of the same handle.  EINVAL for bad arguments or an unbound handle.        */
+invdft_status invdft_initial_guess(invdft_handle h, const double *rho_data, const double *v_H,
+                                   double tau, double alpha, int exchange, double *v_out,
+                                   void *stream);
+
+/* Linear (Q1) v_xc mesh and field transfer (Sec. 3.1.1, Sec. 3.2.2).  The Q1
+ * mesh has nv cells per axis (nv in [1, 4096]) over the handle's box, with
+ * values on all (nv+1)^3 nodes (x fastest); T is the matrix of trilinear
+ * weights of the Q1 interpolant at the handle's unknown nodes (8 per node).
+ * invdft_q1_to_nodes: v_nodes = T v_q1 (the potential seen by the orbitals;
+ *   pass it to invdft_set_potential as v_xc).  v_q1 device [(nv+1)^3],
+ *   v_nodes device [L].
+ * invdft_grad_to_q1: g_q1 = T^T g_nodes, the nodal gradient of Eq. 22 (as
+ *   returned by invdft_loss_grad) pulled back to the Q1 coefficients; each Q1
+ *   node sums its support in a fixed order (deterministic, no atomics).
+ *   g_nodes device [L], g_q1 device [(nv+1)^3].
+ * Both are asynchronous on stream; EINVAL for bad arguments.                */
+invdft_status invdft_q1_to_nodes(invdft_handle h, int nv, const double *v_q1, double *v_nodes,
+                                 void *stream);
+invdft_status invdft_grad_to_q1(invdft_handle h, int nv, const double *g_nodes, double *g_q1,
+                                void *stream);
+
 /* Forget the L-BFGS history and the warm-start orbitals.                   */
 invdft_status invdft_reset(invdft_handle h);
 

@@ -284,6 +284,31 @@ class Problem:
         self.solved_version = self.potential_version
         return st.as_dict()
 
+    def initial_guess(self, rho_data, v_H, tau: float = 1e-2, alpha: float = 1.0,
+                      exchange: str = "lb94"):
+        """v_xc of Eq. 25 (Sec. 4.2.3) from the target density and its Hartree
+        potential (device [L] tensors); exchange "lb94" or "slater"."""
+        v = self.zeros(self.L)
+        _ok("invdft_initial_guess",
+            lib.invdft_initial_guess(self.h, _ptr(rho_data), _ptr(v_H), float(tau), float(alpha),
+                                     {"slater": 0, "lb94": 1}[exchange], _ptr(v), _stream()),
+            self.h, False)
+        return v
+
+    def q1_to_nodes(self, nv: int, v_q1):
+        """v_xc at the unknown nodes from a Q1 field of nv^3 cells (trilinear)."""
+        v = self.zeros(self.L)
+        _ok("invdft_q1_to_nodes", lib.invdft_q1_to_nodes(self.h, int(nv), _ptr(v_q1), _ptr(v),
+                                                         _stream()), self.h, False)
+        return v
+
+    def grad_to_q1(self, nv: int, g_nodes):
+        """A nodal gradient pulled back to the (nv+1)^3 Q1 coefficients (T^T g)."""
+        g = self.zeros((nv + 1) ** 3)
+        _ok("invdft_grad_to_q1", lib.invdft_grad_to_q1(self.h, int(nv), _ptr(g_nodes), _ptr(g),
+                                                       _stream()), self.h, False)
+        return g
+
     def reset(self):
         invdft_reset(self.h)
 

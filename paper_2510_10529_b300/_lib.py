@@ -78,6 +78,9 @@ def _load():
         "invdft_loss_grad": [H, P, P, C.POINTER(C.c_double), P, C.POINTER(Stats), P],
         "invdft_step": [H, P, P, P, C.POINTER(Stats), P],
         "invdft_reset": [H],
+        "invdft_initial_guess": [H, P, P, C.c_double, C.c_double, C.c_int, P, P],
+        "invdft_q1_to_nodes": [H, C.c_int, P, P, P],
+        "invdft_grad_to_q1": [H, C.c_int, P, P, P],
         "invdft_profile_hx": [H, C.c_int, P],
         "invdft_tune_hx": [H, C.c_int, C.c_int, P],
         "invdft_hx_config": [H, C.c_int, C.c_int, P],

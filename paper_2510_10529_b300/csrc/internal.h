@@ -50,6 +50,7 @@ struct Geom {
 struct Tables {
   std::vector<double> gll_x, gll_w;   // q
   std::vector<double> A, B;           // q x q
+  std::vector<double> Dm;             // q x q: l_j'(x_i) at the GLL nodes on [-1, 1]
   std::vector<double> axis;           // node coordinates along one axis, Ni + 2
   std::vector<double> m1;             // 1D lumped mass, Ni + 2
   std::vector<double> kdiag1_A, kdiag1_B;  // assembled 1D diagonals (for the preconditioner)

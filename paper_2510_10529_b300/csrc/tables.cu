@@ -111,6 +111,7 @@ void build_tables(double lo, double hi, int ncell, int p, Tables *t) {
       G[k * q + j] = s;
     }
   }
+  t->Dm = Dm;
   t->A.assign(q * q, 0.0);
   t->B.assign(q * q, 0.0);
   for (int i = 0; i < q; ++i)
