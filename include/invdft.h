@@ -15,10 +15,11 @@
  *     with the far-field mask (Sec. 3.1.2);
  *   - the limited-memory BFGS update of v_xc (Eq. 21).
  *
- * Discretisation (shared by every entry point): a uniform box [lo,hi]^3 cut
- * into ncell^3 cubic cells of order p (2 or 4) with nodes at the
- * Gauss-Lobatto-Legendre points (spectral elements, Sec. 3.2.1).  Boundary
- * nodes carry psi = p = 0; the L = (ncell*p - 1)^3 interior nodes are the
+ * Discretisation (shared by every entry point): a box cut into a tensor
+ * product of box cells of order p (2, 4 or 6) with nodes at the
+ * Gauss-Lobatto-Legendre points (spectral elements, Sec. 3.2.1), equal cells
+ * per axis or graded ones (invdft_mesh_desc).  Boundary nodes carry
+ * psi = p = 0; the L = prod_a (ncell[a] p - 1) interior nodes are the
  * unknowns, numbered lexicographically with x fastest, then y, then z.
  *
  * Data layout: every nodal multivector is node-major ("row-major" in the
@@ -81,11 +82,18 @@ typedef enum {
                            with FP32 accumulation; MINRES stays in FP32         */
 } invdft_precision;
 
-/* Mesh: box [lo,hi]^3, ncell cells per axis, element order (2 or 4). */
+/* Mesh: the box [lo[0],hi[0]] x [lo[1],hi[1]] x [lo[2],hi[2]] (x, y, z) cut
+ * into ncell[0] x ncell[1] x ncell[2] box cells of element order 2, 4 or 6.
+ * breaks[a] (optional, host, ncell[a] + 1 values, copied at create) gives the
+ * cell breaks of axis a, increasing from lo[a] to hi[a], for meshes graded
+ * towards features (Sec. 4.2.2: finer cells near the nuclei); NULL means equal
+ * cells on that axis.  The nodes form a tensor-product grid, so the cell
+ * stiffness keeps its Kronecker form with per-cell scalars (Eq. 17). */
 typedef struct {
-  double lo, hi;
-  int ncell;
+  double lo[3], hi[3];
+  int ncell[3];
   int order;
+  const double *breaks[3];
 } invdft_mesh_desc;
 
 /* Solver options.  Zero fields take the defaults given in brackets.
@@ -150,8 +158,8 @@ invdft_status invdft_set_potential(invdft_handle h, const double *v_fixed_dev,
 
 /* Y = H~ X for an [L][ncol] block (Eq. 19, Sec. 3.2.3), device pointers.
  * prec = INVDFT_FP64: X, Y are double; INVDFT_MIXED (FP32 on the CUDA
- * cores) or INVDFT_MIXED_TF32 (TF32 tensor cores on Q4 meshes): X, Y are
- * float.  Y must not alias X.
+ * cores) or INVDFT_MIXED_TF32 (TF32 tensor cores on uniform cubic Q4 meshes,
+ * the CUDA cores elsewhere): X, Y are float.  Y must not alias X.
  * ncol in [1, 256].  The operator used is the one of the last
  * invdft_set_potential.                                                     */
 invdft_status invdft_apply_h(invdft_handle h, const void *X_dev, void *Y_dev, int ncol,
@@ -209,7 +217,9 @@ invdft_status invdft_step(invdft_handle h, const double *rho_data_dev, const dou
  * adjoint systems of one problem into one block solve (Sec. 3.2.2); this
  * batches whole independent problems (no further counterpart in the paper).
  * invdft_batch_create: handles bound, in INVDFT_MIXED or INVDFT_MIXED_TF32
- * precision, with equal Chebyshev degree in [2, 64] and nstates <= 256;
+ * precision, on uniform cubic meshes (equal box, cells and sizes on every
+ * axis) of order 2 or 4, with equal Chebyshev degree in [2, 64] and nstates
+ * <= 256;
  * n in [1, 64], no handle twice.  The batch keeps the handle pointers: they
  * must outlive it, and no other call may use them while a batch step runs.
  * EINVAL on bad arguments, ECUDA if its streams or device tables cannot be
@@ -255,7 +265,7 @@ invdft_status invdft_batch_set_wait_limit(invdft_batch batch, int polls);
  * events (synchronising on them) and, if out16 != NULL, writes the totals
  * since the last enable: out16[0..3] = FP64 {device ms, algorithmic bytes
  * (X and v read, Z written, plus W/E when present), nominal dense-cell
- * flops 2 (p+1)^6 ncol ncell^3, launches}, out16[4..7] the same for FP32
+ * flops 2 (p+1)^6 ncol cells, launches}, out16[4..7] the same for FP32
  * launches on the CUDA cores that carry the Chebyshev filter's W or E terms,
  * out16[8..11] for the other FP32 CUDA-core launches (the MINRES operator),
  * out16[12..15] for FP32 blocks on the TF32 tensor-core kernel.

@@ -196,9 +196,12 @@ class Problem:
     def __init__(self, lo, hi, ncell, order, nstates, n_electrons=0.0, kT=0.0,
                  prec="fp64", cheb_degree=0, eig_tol=0.0, adj_tol=0.0, tau_bc=0.0,
                  max_cheb_passes=0, max_minres_iters=0, lbfgs_history=0, seed=1,
-                 deg_tol=0.0, device=None):
+                 deg_tol=0.0, device=None, breaks=None):
+        """lo, hi, ncell: scalars for a cube of equal cells, or three values
+        (x, y, z); breaks: optional three sequences of cell breaks (None per
+        axis for equal cells), for graded meshes."""
         self.device = torch.device(device or "cuda")
-        mesh = MeshDesc(lo=float(lo), hi=float(hi), ncell=int(ncell), order=int(order))
+        mesh = MeshDesc.make(lo, hi, ncell, order, breaks)
         opts = Opts(nstates=int(nstates), n_electrons=float(n_electrons), kT=float(kT),
                     cheb_degree=int(cheb_degree), c_eig=0.0, c_ad=0.0, tau_bc=float(tau_bc),
                     eig_tol=float(eig_tol), adj_tol=float(adj_tol),

@@ -22,7 +22,29 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: 
 
 
 class MeshDesc(C.Structure):
-    _fields_ = [("lo", C.c_double), ("hi", C.c_double), ("ncell", C.c_int), ("order", C.c_int)]
+    """invdft_mesh_desc: per-axis box, cells and optional cell breaks."""
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("ncell", C.c_int * 3),
+                ("order", C.c_int), ("breaks", C.POINTER(C.c_double) * 3)]
+
+    @classmethod
+    def make(cls, lo, hi, ncell, order, breaks=None):
+        """lo, hi, ncell: scalars (a cube) or three values (x, y, z); breaks:
+        None or three sequences (None per axis for equal cells)."""
+        three = lambda x, t: [t(v) for v in (x if hasattr(x, "__len__") else (x, x, x))]
+        d = cls()
+        for a, (l, h, n) in enumerate(zip(three(lo, float), three(hi, float), three(ncell, int))):
+            d.lo[a], d.hi[a], d.ncell[a] = l, h, n
+        d.order = int(order)
+        d._keep = []
+        for a in range(3):
+            b = None if breaks is None else breaks[a]
+            if b is None:
+                d.breaks[a] = C.POINTER(C.c_double)()
+            else:
+                arr = (C.c_double * len(b))(*[float(x) for x in b])
+                d._keep.append(arr)
+                d.breaks[a] = C.cast(arr, C.POINTER(C.c_double))
+        return d
 
 
 class Opts(C.Structure):

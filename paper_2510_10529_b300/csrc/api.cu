@@ -71,17 +71,22 @@ bool cuda_ok(Ctx *c, cudaError_t e, const char *what) {
 
 namespace {
 
-__global__ void init_fields(const double *__restrict__ m1, const double *__restrict__ kA,
-                            const double *__restrict__ kB, int Ni, double *__restrict__ mass,
-                            double *__restrict__ dvec, double *__restrict__ prec,
-                            float *__restrict__ precf) {
-  const long long L = (long long)Ni * Ni * Ni;
+struct AxisTabs {
+  const double *m1[3], *kA[3], *kB[3];
+  int n[3];
+};
+
+__global__ void init_fields(AxisTabs t, double *__restrict__ mass, double *__restrict__ dvec,
+                            double *__restrict__ prec, float *__restrict__ precf) {
+  const long long L = (long long)t.n[0] * t.n[1] * t.n[2];
   for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < L;
        a += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(a % Ni) + 1, iy = (int)((a / Ni) % Ni) + 1, iz = (int)(a / ((long long)Ni * Ni)) + 1;
-    const double m = m1[ix] * m1[iy] * m1[iz];
-    const double kaa = 0.5 * (kB[iz] * kB[iy] * kA[ix] + kB[iz] * kA[iy] * kB[ix] +
-                              kA[iz] * kB[iy] * kB[ix]);
+    const int ix = (int)(a % t.n[0]) + 1, iy = (int)((a / t.n[0]) % t.n[1]) + 1;
+    const int iz = (int)(a / ((long long)t.n[0] * t.n[1])) + 1;
+    const double m = t.m1[0][ix] * t.m1[1][iy] * t.m1[2][iz];
+    const double kaa = 0.5 * (t.kB[2][iz] * t.kB[1][iy] * t.kA[0][ix] +
+                              t.kB[2][iz] * t.kA[1][iy] * t.kB[0][ix] +
+                              t.kA[2][iz] * t.kB[1][iy] * t.kB[0][ix]);
     mass[a] = m;
     dvec[a] = 1.0 / sqrt(m);
     prec[a] = m / kaa;          // inverse diagonal of D K D (Laplacian part)
@@ -107,19 +112,24 @@ size_t plan(Ctx *c, char *base) {
   ar.base = base;
   const long long L = c->L;
   const int nv = c->nv;
-  const int N = c->g.Ni + 2;
   const size_t blk = (size_t)L * nv;
-  c->dm1 = ar.take<double>(N);
-  c->dm1f = ar.take<float>(N);
-  c->m1tab = ar.take<double>(N);
-  c->kAtab = ar.take<double>(N);
-  c->kBtab = ar.take<double>(N);
+  for (int a = 0; a < 3; ++a) {
+    const int N = c->g.n[a] + 2, nc = c->g.nc[a];
+    c->dnode[a] = ar.take<double>(N);
+    c->m1tab[a] = ar.take<double>(N);
+    c->kAtab[a] = ar.take<double>(N);
+    c->kBtab[a] = ar.take<double>(N);
+    c->axis[a] = ar.take<double>(N);
+    c->cellA[a] = ar.take<double>(nc);
+    c->cellB[a] = ar.take<double>(nc);
+  }
+  c->dm1f = ar.take<float>(c->g.n[0] + 2);
   c->mass = ar.take<double>(L);
   c->dvec = ar.take<double>(L);
   c->prec_diag = ar.take<double>(L);
   c->precf = ar.take<float>(L);
   c->Ke_tc = ar.take<float>(tc_cell_matrix_floats());
-  c->cell_perm = ar.take<int>((size_t)c->g.ncell * c->g.ncell * c->g.ncell);
+  c->cell_perm = ar.take<int>(c->g.cube ? (size_t)c->g.ncell * c->g.ncell * c->g.ncell : 1);
   c->v = ar.take<double>(L);
   c->vf = ar.take<float>(L);
   c->vfixed = ar.take<double>(L);
@@ -167,17 +177,33 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
     return INVDFT_EINVAL;
   }
   *out = nullptr;
-  if (!(mesh->order == 2 || mesh->order == 4) || mesh->ncell < 1 || !(mesh->hi > mesh->lo)) {
-    g_create_error = "create_mesh: order must be 2 or 4, ncell >= 1, hi > lo";
+  if (!(mesh->order == 2 || mesh->order == 4 || mesh->order == 6)) {
+    g_create_error = "create_mesh: order must be 2, 4 or 6";
     return INVDFT_EINVAL;
   }
-  const long long Ni = (long long)mesh->ncell * mesh->order - 1;
-  if (Ni < 1 || Ni > 2047) {
-    g_create_error = "create_mesh: mesh has no unknowns or is too large";
-    return INVDFT_EINVAL;
+  long long nn[3];
+  for (int a = 0; a < 3; ++a) {
+    if (mesh->ncell[a] < 1 || !(mesh->hi[a] > mesh->lo[a])) {
+      g_create_error = "create_mesh: every axis needs ncell >= 1 and hi > lo";
+      return INVDFT_EINVAL;
+    }
+    nn[a] = (long long)mesh->ncell[a] * mesh->order - 1;
+    if (nn[a] < 1 || nn[a] > 4095) {
+      g_create_error = "create_mesh: an axis has no unknowns or more than 4095";
+      return INVDFT_EINVAL;
+    }
+    if (mesh->breaks[a]) {
+      const double *b = mesh->breaks[a];
+      bool ok = b[0] == mesh->lo[a] && b[mesh->ncell[a]] == mesh->hi[a];
+      for (int e = 0; e < mesh->ncell[a] && ok; ++e) ok = b[e + 1] > b[e];
+      if (!ok) {
+        g_create_error = "create_mesh: breaks must increase from lo to hi";
+        return INVDFT_EINVAL;
+      }
+    }
   }
-  if (Ni * Ni * Ni * (long long)kMaxCols >= (1LL << 31)) {
-    g_create_error = "create_mesh: (ncell*order-1)^3 * 256 must stay below 2^31";
+  if (nn[0] * nn[1] * nn[2] * (long long)kMaxCols >= (1LL << 31)) {
+    g_create_error = "create_mesh: unknowns * 256 must stay below 2^31";
     return INVDFT_EINVAL;
   }
   if (opts->nstates < 1 || opts->nstates > kMaxDense) {
@@ -189,7 +215,6 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
     g_create_error = "create_mesh: out of host memory";
     return INVDFT_ENOMEM;
   }
-  c->mesh = *mesh;
   c->o = *opts;
   invdft_opts &o = c->o;
   if (o.cheb_degree <= 0) o.cheb_degree = 20;
@@ -202,26 +227,42 @@ invdft_status invdft_create_mesh(const invdft_mesh_desc *mesh, const invdft_opts
   if (o.deg_tol <= 0) o.deg_tol = 1e-8;
   if (o.kT < 0) o.kT = 0;
   c->nv = o.nstates;
-  build_tables(mesh->lo, mesh->hi, mesh->ncell, mesh->order, &c->tab);
+  build_reference(mesh->order, &c->tab);
   Geom &g = c->g;
   g.p = mesh->order;
   g.q = mesh->order + 1;
-  g.ncell = mesh->ncell;
-  g.Ni = (int)Ni;
-  g.L = Ni * Ni * Ni;
-  g.kc = 0.25 * (mesh->hi - mesh->lo) / mesh->ncell;
   for (int i = 0; i < g.q * g.q; ++i) {
     g.A[i] = c->tab.A[i];
     g.B[i] = c->tab.B[i];
   }
-  for (int ax = 0; ax < 3; ++ax) {
-    const double sh = 0.5 * (mesh->hi - mesh->lo) / mesh->ncell;
-    g.s[ax] = sh;
+  g.graded = false;
+  for (int a = 0; a < 3; ++a) {
+    const int nc = mesh->ncell[a];
+    std::vector<double> br(nc + 1);
+    for (int e = 0; e <= nc; ++e)
+      br[e] = mesh->breaks[a] ? mesh->breaks[a][e]
+                              : (e == nc ? mesh->hi[a]
+                                         : mesh->lo[a] + (mesh->hi[a] - mesh->lo[a]) * e / nc);
+    build_axis(c->tab, br, g.p, &c->tab.ax[a]);
+    g.nc[a] = nc;
+    g.n[a] = (int)nn[a];
+    g.graded |= !c->tab.ax[a].uniform;
+    const double sh = 0.5 * (mesh->hi[a] - mesh->lo[a]) / nc;
+    g.s[a] = sh;
     for (int i = 0; i <= g.p; ++i) {
       const double m = (i == 0 || i == g.p) ? 2.0 * sh * c->tab.gll_w[0] : sh * c->tab.gll_w[i];
-      g.dl[ax][i] = 1.0 / std::sqrt(m);
+      g.dl[a][i] = 1.0 / std::sqrt(m);
     }
   }
+  g.cube = !g.graded && g.nc[0] == g.nc[1] && g.nc[1] == g.nc[2] &&
+           std::fabs(g.s[0] - g.s[1]) <= 1e-14 * g.s[0] &&
+           std::fabs(g.s[1] - g.s[2]) <= 1e-14 * g.s[0];
+  g.ncell = g.nc[0];
+  g.Ni = g.n[0];
+  g.L = nn[0] * nn[1] * nn[2];
+  g.kc = 0.5 * g.s[0];
+  c->mesh = *mesh;
+  for (int a = 0; a < 3; ++a) c->mesh.breaks[a] = nullptr;   // copied into the tables
   c->L = g.L;
   c->ws_bytes = plan(c, nullptr);
   *out = c;
@@ -263,29 +304,52 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   }
   plan(h, base);
   if (!h->hbuf) INV_CUDA(h, cudaHostAlloc((void **)&h->hbuf, 16 * kMaxCols * sizeof(double), 0));
-  // 1D tables: 1/sqrt(m1) (zero at the Dirichlet ends), m1, assembled diagonals
-  const int N = h->g.Ni + 2;
-  std::vector<double> dm1(N), tabs(3 * (size_t)N);
-  for (int i = 0; i < N; ++i) {
-    dm1[i] = (i == 0 || i == N - 1) ? 0.0 : 1.0 / std::sqrt(h->tab.m1[i]);
-    tabs[i] = h->tab.m1[i];
-    tabs[N + i] = h->tab.kdiag1_A[i];
-    tabs[2 * N + i] = h->tab.kdiag1_B[i];
+  // 1D tables per axis: 1/sqrt(m1) (zero at the Dirichlet ends), m1, assembled
+  // diagonals, node coordinates, and the cell scalars 2/h_e and h_e/2
+  std::vector<std::vector<double>> host;     // kept alive until the stream sync below
+  AxisTabs at;
+  for (int a = 0; a < 3; ++a) {
+    const AxisTab &t = h->tab.ax[a];
+    const int N = h->g.n[a] + 2, nc = h->g.nc[a];
+    std::vector<double> dn(N), ca(nc), cb(nc);
+    for (int i = 0; i < N; ++i) dn[i] = (i == 0 || i == N - 1) ? 0.0 : 1.0 / std::sqrt(t.m1[i]);
+    for (int e = 0; e < nc; ++e) {
+      ca[e] = 2.0 / t.h[e];
+      cb[e] = 0.5 * t.h[e];
+    }
+    host.push_back(dn);
+    host.push_back(ca);
+    host.push_back(cb);
+    auto up = [&](double *dst, const std::vector<double> &src) {
+      return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice,
+                             s);
+    };
+    INV_CUDA(h, up(h->dnode[a], host[host.size() - 3]));
+    INV_CUDA(h, up(h->cellA[a], host[host.size() - 2]));
+    INV_CUDA(h, up(h->cellB[a], host[host.size() - 1]));
+    INV_CUDA(h, up(h->m1tab[a], t.m1));
+    INV_CUDA(h, up(h->kAtab[a], t.kdiag1_A));
+    INV_CUDA(h, up(h->kBtab[a], t.kdiag1_B));
+    INV_CUDA(h, up(h->axis[a], t.axis));
+    at.m1[a] = h->m1tab[a];
+    at.kA[a] = h->kAtab[a];
+    at.kB[a] = h->kBtab[a];
+    at.n[a] = h->g.n[a];
+    h->g.dnode[a] = h->dnode[a];
+    h->g.m1node[a] = h->m1tab[a];
+    h->g.cellA[a] = h->cellA[a];
+    h->g.cellB[a] = h->cellB[a];
+    h->g.axis[a] = h->axis[a];
   }
-  double *m1 = h->m1tab, *kA = h->kAtab, *kB = h->kBtab;
-  INV_CUDA(h, cudaMemcpyAsync(h->dm1, dm1.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
-  std::vector<float> dm1f(dm1.begin(), dm1.end());
-  INV_CUDA(h, cudaMemcpyAsync(h->dm1f, dm1f.data(), N * sizeof(float), cudaMemcpyHostToDevice, s));
-  INV_CUDA(h, cudaMemcpyAsync(m1, tabs.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
-  INV_CUDA(h, cudaMemcpyAsync(kA, tabs.data() + N, N * sizeof(double), cudaMemcpyHostToDevice, s));
-  INV_CUDA(h, cudaMemcpyAsync(kB, tabs.data() + 2 * N, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  std::vector<float> dm1f(host[0].begin(), host[0].end());
+  INV_CUDA(h, cudaMemcpyAsync(h->dm1f, dm1f.data(), dm1f.size() * sizeof(float),
+                              cudaMemcpyHostToDevice, s));
   ::invdft::count_launch();
-  init_fields<<<grid_for(h->L), 256, 0, s>>>(m1, kA, kB, h->g.Ni, h->mass, h->dvec, h->prec_diag,
-                                             h->precf);
+  init_fields<<<grid_for(h->L), 256, 0, s>>>(at, h->mass, h->dvec, h->prec_diag, h->precf);
   INV_LAUNCH(h, "init_fields");
   std::vector<float> ke;
   std::vector<int> perm;
-  if (h->g.p == 4) {
+  if (h->g.p == 4 && h->g.cube) {
     build_tc_cell_matrix(h->g, &ke);
     INV_CUDA(h, cudaMemcpyAsync(h->Ke_tc, ke.data(), ke.size() * sizeof(float),
                                 cudaMemcpyHostToDevice, s));
@@ -294,13 +358,14 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
                                 cudaMemcpyHostToDevice, s));
   } else {
     h->Ke_tc = nullptr;
+    h->cell_perm = nullptr;
   }
   INV_CUDA(h, cudaMemsetAsync(h->status, 0, 16 * sizeof(int), s));
   INV_CUDA(h, cudaMemsetAsync(h->v, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaMemsetAsync(h->vf, 0, h->L * sizeof(float), s));
   INV_CUDA(h, cudaMemsetAsync(h->vfixed, 0, h->L * sizeof(double), s));
   INV_CUDA(h, cudaStreamSynchronize(s));   // host tables above are freed on return
-  h->g.dm1 = h->dm1;
+  h->g.dm1 = h->dnode[0];
   h->g.dm1f = h->dm1f;
   h->bound = true;
   h->have_potential = false;
@@ -314,15 +379,15 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
 
 invdft_status invdft_node_coords(invdft_handle h, double *xyz) {
   if (!h || !xyz) return INVDFT_EINVAL;
-  const int Ni = h->g.Ni;
-  const std::vector<double> &ax = h->tab.axis;
+  const std::vector<double> &axx = h->tab.ax[0].axis, &axy = h->tab.ax[1].axis,
+                            &axz = h->tab.ax[2].axis;
   long long a = 0;
-  for (int iz = 1; iz <= Ni; ++iz)
-    for (int iy = 1; iy <= Ni; ++iy)
-      for (int ix = 1; ix <= Ni; ++ix, ++a) {
-        xyz[3 * a + 0] = ax[ix];
-        xyz[3 * a + 1] = ax[iy];
-        xyz[3 * a + 2] = ax[iz];
+  for (int iz = 1; iz <= h->g.n[2]; ++iz)
+    for (int iy = 1; iy <= h->g.n[1]; ++iy)
+      for (int ix = 1; ix <= h->g.n[0]; ++ix, ++a) {
+        xyz[3 * a + 0] = axx[ix];
+        xyz[3 * a + 1] = axy[iy];
+        xyz[3 * a + 2] = axz[iz];
       }
   return INVDFT_OK;
 }

@@ -340,8 +340,10 @@ invdft_status invdft_batch_create(const invdft_handle *handles, int n, invdft_ba
   *out = nullptr;
   for (int b = 0; b < n; ++b) {
     const Ctx *c = handles[b];
+    // the persistent filter kernel covers uniform cubic meshes of order 2 or 4
     if (!c || !c->bound || c->o.prec == INVDFT_FP64 || c->o.cheb_degree != handles[0]->o.cheb_degree ||
-        c->o.cheb_degree < 2 || c->o.cheb_degree > kMaxBatchDeg || c->nv > 256)
+        c->o.cheb_degree < 2 || c->o.cheb_degree > kMaxBatchDeg || c->nv > 256 || !c->g.cube ||
+        !(c->g.p == 2 || c->g.p == 4))
       return INVDFT_EINVAL;
     for (int j = 0; j < b; ++j)
       if (handles[j] == handles[b]) return INVDFT_EINVAL;

@@ -28,7 +28,7 @@ constexpr double kLb94Beta = 0.05;
 struct GuessGeom {
   int n[3];          // unknowns per axis (x, y, z)
   int p;
-  double dscale[3];  // 2 / h per axis (reference derivative to physical)
+  const double *cellA[3];    // 2 / h_e per cell and axis (reference derivative to physical)
   double D[kMaxQ * kMaxQ];   // D[i][j] = l_j'(x_i) on [-1, 1]
 };
 
@@ -42,7 +42,7 @@ __device__ __forceinline__ double axis_derivative(const GuessGeom &G, int axis, 
   if (l != 0) {
     double s = 0.0;
     for (int j = 0; j < q; ++j) s += G.D[l * q + j] * at(e * p + j);
-    return s * G.dscale[axis];
+    return s * G.cellA[axis][e];
   }
   // a cell vertex (never the boundary: 1 <= g <= n): mean of the left cell's
   // derivative at its local node p and the right cell's at its local node 0
@@ -51,7 +51,7 @@ __device__ __forceinline__ double axis_derivative(const GuessGeom &G, int axis, 
     sl += G.D[p * q + j] * at((e - 1) * p + j);
     sr += G.D[j] * at(e * p + j);
   }
-  return 0.5 * (sl + sr) * G.dscale[axis];
+  return 0.5 * (sl * G.cellA[axis][e - 1] + sr * G.cellA[axis][e]);
 }
 
 __global__ void gradnorm_kernel(const double *__restrict__ rho, GuessGeom G, double *__restrict__ gn) {
@@ -134,8 +134,8 @@ extern "C" invdft_status invdft_initial_guess(invdft_handle h, const double *rho
     GuessGeom G;
     G.p = h->g.p;
     for (int ax = 0; ax < 3; ++ax) {
-      G.n[ax] = h->g.Ni;
-      G.dscale[ax] = 1.0 / h->g.s[ax];
+      G.n[ax] = h->g.n[ax];
+      G.cellA[ax] = h->g.cellA[ax];
     }
     const int q = h->g.p + 1;
     for (int i = 0; i < q * q; ++i) G.D[i] = h->tab.Dm[i];

@@ -116,6 +116,8 @@ __device__ __forceinline__ void eo_apply(const T *e1, const T *o1, const T *eM1,
 }
 
 // One CTA per (cell, chunk of C columns).  Two shared buffers of (p+1)^3 x C.
+// The cell's per-axis scalars (2/h_a for A, h_a/2 for B) scale each 1D
+// contraction, so box cells of any size (graded meshes) take the same path.
 template <typename T, int P, int C>
 __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__restrict__ Z,
                                                 int ncol, Geom g, EoTab<P> tab, double scale) {
@@ -128,10 +130,12 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
   __shared__ double dl[3][Q];
   __shared__ int gidx[3][Q];
 
-  const int nc = g.ncell, Ni = g.Ni;
   const int cell = blockIdx.x;
-  const int cx = cell % nc, cy = (cell / nc) % nc, cz = cell / (nc * nc);
+  const int cx = cell % g.nc[0], cy = (cell / g.nc[0]) % g.nc[1], cz = cell / (g.nc[0] * g.nc[1]);
   const int c0 = blockIdx.y * C;
+  const T sAx = (T)g.cellA[0][cx], sBx = (T)g.cellB[0][cx];
+  const T sAy = (T)g.cellA[1][cy], sBy = (T)g.cellB[1][cy];
+  const T sAz = (T)g.cellA[2][cz], sBz = (T)g.cellB[2][cz];
   const int tid = threadIdx.x;
 
   if (tid < NEC) {
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     const int d = tid / Q, l = tid % Q;
     const int c = d == 0 ? cx : (d == 1 ? cy : cz);
     const int gi = c * P + l;                 // full-grid index along the axis
-    dl[d][l] = g.dm1[gi];                     // 0 on the boundary
-    gidx[d][l] = (gi >= 1 && gi <= Ni) ? gi - 1 : -1;
+    dl[d][l] = g.dnode[d][gi];                // 0 on the boundary
+    gidx[d][l] = (gi >= 1 && gi <= g.n[d]) ? gi - 1 : -1;
   }
   __syncthreads();
 
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     const int ix = gidx[0][lx], iy = gidx[1][ly], iz = gidx[2][lz];
     T val = (T)0;
     if (ix >= 0 && iy >= 0 && iz >= 0 && c0 + j < ncol) {
-      const long long node = ix + (long long)Ni * (iy + (long long)Ni * iz);
+      const long long node = ix + (long long)g.n[0] * (iy + (long long)g.n[1] * iz);
       val = (T)(dl[0][lx] * dl[1][ly] * dl[2][lz]) * X[node * ncol + c0 + j];
     }
     u[idx] = val;
@@ -177,8 +181,8 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     eo_apply<T, P, false>(e, o, eA, oA, e, o, eA, oA, ya);
 #pragma unroll
     for (int xo = 0; xo < Q; ++xo) {
-      u[(base + xo) * C + j] = yb[xo];
-      w[(base + xo) * C + j] = ya[xo];
+      u[(base + xo) * C + j] = sBx * yb[xo];
+      w[(base + xo) * C + j] = sAx * ya[xo];
     }
   }
   __syncthreads();
@@ -195,12 +199,14 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     }
     eo_split<T, P>(t1, e1, o1);
     eo_split<T, P>(t2, e2, o2);
+    T ya[Q];
     eo_apply<T, P, false>(e1, o1, eB, oB, e1, o1, eB, oB, y1);
-    eo_apply<T, P, true>(e1, o1, eA, oA, e2, o2, eB, oB, y2);
+    eo_apply<T, P, false>(e1, o1, eA, oA, e1, o1, eA, oA, ya);
+    eo_apply<T, P, false>(e2, o2, eB, oB, e2, o2, eB, oB, y2);
 #pragma unroll
     for (int yo = 0; yo < Q; ++yo) {
-      u[(x + Q * (yo + Q * z)) * C + j] = y1[yo];
-      w[(x + Q * (yo + Q * z)) * C + j] = y2[yo];
+      u[(x + Q * (yo + Q * z)) * C + j] = sBy * y1[yo];
+      w[(x + Q * (yo + Q * z)) * C + j] = sAy * ya[yo] + sBy * y2[yo];
     }
   }
   __syncthreads();
@@ -217,9 +223,11 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     }
     eo_split<T, P>(t1, e1, o1);
     eo_split<T, P>(t2, e2, o2);
-    eo_apply<T, P, true>(e1, o1, eA, oA, e2, o2, eB, oB, yz);
+    T yb[Q];
+    eo_apply<T, P, false>(e1, o1, eA, oA, e1, o1, eA, oA, yz);
+    eo_apply<T, P, false>(e2, o2, eB, oB, e2, o2, eB, oB, yb);
 #pragma unroll
-    for (int zo = 0; zo < Q; ++zo) u[(x + Q * (y + Q * zo)) * C + j] = yz[zo];
+    for (int zo = 0; zo < Q; ++zo) u[(x + Q * (y + Q * zo)) * C + j] = sAz * yz[zo] + sBz * yb[zo];
   }
   __syncthreads();
 
@@ -229,7 +237,7 @@ __global__ void __launch_bounds__(256) hx_cells(const T *__restrict__ X, T *__re
     const int lx = a % Q, ly = (a / Q) % Q, lz = a / (Q * Q);
     const int ix = gidx[0][lx], iy = gidx[1][ly], iz = gidx[2][lz];
     if (ix >= 0 && iy >= 0 && iz >= 0 && c0 + j < ncol) {
-      const long long node = ix + (long long)Ni * (iy + (long long)Ni * iz);
+      const long long node = ix + (long long)g.n[0] * (iy + (long long)g.n[1] * iz);
       const T val = (T)(scale * dl[0][lx] * dl[1][ly] * dl[2][lz]) * u[idx];
       atomic_add(&Z[node * ncol + c0 + j], val);
     }
@@ -243,7 +251,7 @@ cudaError_t run_cells(const Geom &g, const T *X, T *Z, int ncol, double scale, c
   auto k = hx_cells<T, P, C>;
   cudaError_t e = raise_smem_limit(k, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(g.ncell * g.ncell * g.ncell, (ncol + C - 1) / C);
+  dim3 grid(g.nc[0] * g.nc[1] * g.nc[2], (ncol + C - 1) / C);
   ::invdft::count_launch();
   k<<<grid, 256, smem, s>>>(X, Z, ncol, g, make_eo<P>(g), scale);
   return cudaGetLastError();
@@ -266,9 +274,11 @@ cudaError_t launch_hx_t(const Geom &g, const double *v, const HxArgs<T> &a, cuda
                                      a.beta, a.E, a.escale, make_fastdiv(a.ncol));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double scale = a.alpha * g.kc;
+  // K_e = 1/2 (B_z B_y A_x + B_z A_y B_x + A_z B_y B_x) with the cell scalars
+  const double scale = 0.5 * a.alpha;
   if (g.p == 2) return run_cells_p<T, 2>(g, a.X, a.Z, a.ncol, scale, s);
   if (g.p == 4) return run_cells_p<T, 4>(g, a.X, a.Z, a.ncol, scale, s);
+  if (g.p == 6) return run_cells_p<T, 6>(g, a.X, a.Z, a.ncol, scale, s);
   return cudaErrorInvalidValue;
 }
 
@@ -308,7 +318,7 @@ bool uses_sweep(const Ctx *c, const HxArgs<T> &a) {
 // (variant 0, the whole z range).
 template <typename T>
 std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStream_t s) {
-  const int nc = c->g.ncell, nvar = sweep_variants(c->g, sizeof(T));
+  const int nc = c->g.nc[2], nvar = sweep_variants(c->g, sizeof(T));
   const int fv = c->hx_variant_fixed < nvar ? c->hx_variant_fixed : -1;
   const int fs = c->hx_seglen_fixed > 0 ? std::min(c->hx_seglen_fixed, nc) : 0;
   if (fv >= 0 && fs > 0) return {fv, fs};
@@ -401,7 +411,7 @@ cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   if (a.W) bytes += n * sz * L;
   if (a.E) bytes += n * 4.0 * L;
   const double ne = (double)c->g.q * c->g.q * c->g.q;
-  const double cells = (double)c->g.ncell * c->g.ncell * c->g.ncell;
+  const double cells = (double)c->g.nc[0] * c->g.nc[1] * c->g.nc[2];
   p.kind[k] = kind;
   p.bytes[k] = bytes;
   p.flops[k] = 2.0 * ne * ne * n * cells;

@@ -1,5 +1,5 @@
 // H~X in the owner-computes sweep form (Eq. 17, Eq. 19, Sec. 3.2.3), FP32 and
-// FP64, for tensor-product meshes of order p in {2, 4}.
+// FP64, for tensor-product meshes of order p in {2, 4, 6}, equal or graded cells.
 //
 // On a tensor-product mesh the cell matrix is a sum of Kronecker products,
 // K_e = 1/2 (B_z (x) B_y (x) A_x + B_z (x) A_y (x) B_x + A_z (x) B_y (x) B_x),
@@ -66,6 +66,7 @@ __device__ __forceinline__ float2 vfma(float a, float2 x, float2 y) {
 __device__ __forceinline__ double2 vfma(double a, double2 x, double2 y) {
   return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
 }
+__device__ __forceinline__ float2 vmul(float a, float2 x) { return __fmul2_rn(make_float2(a, a), x); }
 __device__ __forceinline__ double2 vmul(double a, double2 x) { return make_double2(a * x.x, a * x.y); }
 __device__ __forceinline__ float2 vadd(float2 x, float2 y) { return __fadd2_rn(x, y); }
 __device__ __forceinline__ double2 vadd(double2 x, double2 y) {
@@ -161,8 +162,11 @@ struct SweepArgs {
   double shift, alpha, beta;
   int *err;                   // set to 3 when a wait for a TMA plane gives up
   int ncol, nx, ny, nz;       // columns; unknowns per axis
-  int ncz;                    // cells along z
+  int ncx, ncy, ncz;          // cells per axis
   int ntx, nty, nchunk, seglen;
+  // graded meshes: per axis m1^-1/2 and m1 at every node (boundary included)
+  // and the cell scalars 2/h_e (A) and h_e/2 (B)
+  const double *dn[3], *m1[3], *cA[3], *cB[3];
 };
 
 // tile shape of a variant
@@ -279,8 +283,12 @@ __device__ __forceinline__ V row0(const V *e, const V *o, const CT *eM, const CT
   return acc;
 }
 
+// GR (graded meshes): the cell blocks are not all equal, so the coefficients
+// are the reference blocks; X is scaled by D = d_x d_y d_z as it enters the x
+// sweep, each cell's outputs by its scalars 2/h_e (A) or h_e/2 (B), and the
+// result by D at the output (the nodal term is carried divided by D).
 template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
-          bool HE>
+          bool HE, bool GR>
 __global__ void __launch_bounds__(SweepShape<T, P, C, TX, TY, XPT, VW>::NTH, MINB)
 hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::type, P> p,
                 const __grid_constant__ CUtensorMap tmx) {
@@ -343,6 +351,17 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
   const bool cx_in = ux < p.nx && colp < p.ncol;
   const V ash = vload<V>(sash + VW * cv), esc = vload<V>(sesc + VW * cv);
   const T alpha = (T)p.alpha, beta = (T)p.beta;
+  // graded meshes: D and D^-1 = sqrt(m) of the thread's nodes in x and y
+  T dxy[P], sxy[P];
+  if constexpr (GR) {
+    const int gx = min(ux + 1, p.nx + 1);
+#pragma unroll
+    for (int yi = 0; yi < P; ++yi) {
+      const int gy = min(gy0 + jy * P + yi + 1, p.ny + 1);
+      dxy[yi] = (T)(p.dn[0][gx] * p.dn[1][gy]);
+      sxy[yi] = (T)(p.m1[0][gx] * p.dn[0][gx] * p.m1[1][gy] * p.dn[1][gy]);
+    }
+  }
   V acc[P + 1][P];
 #pragma unroll
   for (int i = 0; i <= P; ++i)
@@ -358,6 +377,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       if (cx_in && uy < p.ny) {
         const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
         V val = a[yi];
+        if constexpr (GR) val = vmul((T)(dxy[yi] * p.dn[2][g]), val);
         if (HW) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
         if constexpr (HE) val = vfmav(esc, eload<V>(p.E + off), val);
         *reinterpret_cast<V *>(p.Z + off) = val;
@@ -368,38 +388,68 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
   // x sweep of one plane: Px = A^x X, Qx = B^x X at the owned x of every row;
   // a task takes XPT consecutive x-cells of a row (the shared vertices are
   // summed in registers) and row 0 of the cell after them
-  auto xsweep = [&](const V *xs, V *Pw, V *Qw) {
+  auto xsweep = [&](const V *xs, V *Pw, V *Qw, int gzp) {
+    const T dz = GR ? (T)p.dn[2][gzp] : (T)1;
     for (int t = tid; t < S::NTASKX; t += NTH) {
       const int xcv = t % NCP;
       const int rest = t / NCP;
       const int r = rest % RY;
       const int jt = rest / RY;
       const V *src = xs + (r * RX + jt * XPT * P) * NCP + xcv;
+      // graded meshes: D of the inputs along this row, and the x-cells' scalars
+      T drow = (T)1;
+      int ex0 = 0;
+      if constexpr (GR) {
+        drow = (T)p.dn[1][min(gy0 + r, p.ny + 1)] * dz;
+        ex0 = gx0 / P + jt * XPT;
+      }
+      auto load_in = [&](V *u, int c) {
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+          u[i] = src[(c + i) * NCP];
+          if constexpr (GR)
+            u[i] = vmul((T)(drow * p.dn[0][min(gx0 + jt * XPT * P + c + i, p.nx + 1)]), u[i]);
+        }
+      };
       V pa[XPT * P], qb[XPT * P];
 #pragma unroll
       for (int q = 0; q < XPT; ++q) {
         V u[P + 1], e[H + 1], o[H > 0 ? H : 1];
-#pragma unroll
-        for (int i = 0; i <= P; ++i) u[i] = src[(q * P + i) * NCP];
+        load_in(u, q * P);
         split<P>(u, e, o);
-        if (q == 0) {
-          apply_hi<P, false, false>(e, o, cf.eAx, cf.oAx, e, o, cf.eAx, cf.oAx, pa, pa);
-          apply_hi<P, false, false>(e, o, cf.eBx, cf.oBx, e, o, cf.eBx, cf.oBx, qb, qb);
-        } else {
-          V la, lb;
-          apply_hi<P, false, true>(e, o, cf.eAx, cf.oAx, e, o, cf.eAx, cf.oAx, pa + q * P, &la);
-          apply_hi<P, false, true>(e, o, cf.eBx, cf.oBx, e, o, cf.eBx, cf.oBx, qb + q * P, &lb);
+        V la, lb;
+        apply_hi<P, false, true>(e, o, cf.eAx, cf.oAx, e, o, cf.eAx, cf.oAx, pa + q * P, &la);
+        apply_hi<P, false, true>(e, o, cf.eBx, cf.oBx, e, o, cf.eBx, cf.oBx, qb + q * P, &lb);
+        if constexpr (GR) {
+          const int ec = min(ex0 + q, p.ncx - 1);
+          const T sa = (T)p.cA[0][ec], sb = (T)p.cB[0][ec];
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            pa[q * P + i] = vmul(sa, pa[q * P + i]);
+            qb[q * P + i] = vmul(sb, qb[q * P + i]);
+          }
+          la = vmul(sa, la);
+          lb = vmul(sb, lb);
+        }
+        if (q > 0) {
           pa[q * P - 1] = vadd(pa[q * P - 1], la);
           qb[q * P - 1] = vadd(qb[q * P - 1], lb);
         }
       }
       {
         V u[P + 1], e[H + 1], o[H > 0 ? H : 1];
-#pragma unroll
-        for (int i = 0; i <= P; ++i) u[i] = src[(XPT * P + i) * NCP];
+        load_in(u, XPT * P);
         split<P>(u, e, o);
-        pa[XPT * P - 1] = row0<P>(e, o, cf.eAx, cf.oAx, pa[XPT * P - 1]);
-        qb[XPT * P - 1] = row0<P>(e, o, cf.eBx, cf.oBx, qb[XPT * P - 1]);
+        if constexpr (GR) {
+          const int ec = min(ex0 + XPT, p.ncx - 1);
+          pa[XPT * P - 1] = vfma((T)p.cA[0][ec], row0<P>(e, o, cf.eAx, cf.oAx, vzero<V>()),
+                                 pa[XPT * P - 1]);
+          qb[XPT * P - 1] = vfma((T)p.cB[0][ec], row0<P>(e, o, cf.eBx, cf.oBx, vzero<V>()),
+                                 qb[XPT * P - 1]);
+        } else {
+          pa[XPT * P - 1] = row0<P>(e, o, cf.eAx, cf.oAx, pa[XPT * P - 1]);
+          qb[XPT * P - 1] = row0<P>(e, o, cf.eBx, cf.oBx, qb[XPT * P - 1]);
+        }
       }
       V *dp = Pw + r * PXS + jt * XPT * P * NCP + xcv;
       V *dq = Qw + r * PXS + jt * XPT * P * NCP + xcv;
@@ -413,7 +463,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
 
   // prologue: x sweep of the first plane
   if (!wait_parity(&full[0], 0u)) abort_flag = 1;
-  xsweep(stage0, Px, Qx);
+  xsweep(stage0, Px, Qx, gz_begin);
   __syncthreads();
   // One barrier per plane: the y / z work of plane it (reading Px / Qx buffer
   // it & 1 and the X stage of plane it) and the x sweep of plane it + 1 (into
@@ -452,8 +502,23 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       }
       split<P>(u, eu, ou);
       split<P>(w, ew, ow);
-      apply_hi<P, true, false>(eu, ou, cf.eBy, cf.oBy, ew, ow, cf.eAy, cf.oAy, R, R);
-      apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
+      if constexpr (GR) {
+        // R = s_B B Px + s_A A Qx, S = s_B B Qx with the y-cell's scalars
+        const int ey = min((gy0 + jy * P) / P, p.ncy - 1);
+        const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
+        V Ra[P], Rb[P];
+        apply_hi<P, false, false>(eu, ou, cf.eBy, cf.oBy, eu, ou, cf.eBy, cf.oBy, Rb, Rb);
+        apply_hi<P, false, false>(ew, ow, cf.eAy, cf.oAy, ew, ow, cf.eAy, cf.oAy, Ra, Ra);
+        apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          R[i] = vfma(sb, Rb[i], vmul(sa, Ra[i]));
+          Sv[i] = vmul(sb, Sv[i]);
+        }
+      } else {
+        apply_hi<P, true, false>(eu, ou, cf.eBy, cf.oBy, ew, ow, cf.eAy, cf.oAy, R, R);
+        apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
+      }
 #pragma unroll
       for (int i = 0; i <= P; ++i) {
         u[i] = sp[(P + i) * PXS];
@@ -461,8 +526,16 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       }
       split<P>(u, eu, ou);
       split<P>(w, ew, ow);
-      R[P - 1] = row0<P>(ew, ow, cf.eAy, cf.oAy, row0<P>(eu, ou, cf.eBy, cf.oBy, R[P - 1]));
-      Sv[P - 1] = row0<P>(ew, ow, cf.eBy, cf.oBy, Sv[P - 1]);
+      if constexpr (GR) {
+        const int ey = min((gy0 + jy * P) / P + 1, p.ncy - 1);
+        const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
+        R[P - 1] = vfma(sb, row0<P>(eu, ou, cf.eBy, cf.oBy, vzero<V>()), R[P - 1]);
+        R[P - 1] = vfma(sa, row0<P>(ew, ow, cf.eAy, cf.oAy, vzero<V>()), R[P - 1]);
+        Sv[P - 1] = vfma(sb, row0<P>(ew, ow, cf.eBy, cf.oBy, vzero<V>()), Sv[P - 1]);
+      } else {
+        R[P - 1] = row0<P>(ew, ow, cf.eAy, cf.oAy, row0<P>(eu, ou, cf.eBy, cf.oBy, R[P - 1]));
+        Sv[P - 1] = row0<P>(ew, ow, cf.eBy, cf.oBy, Sv[P - 1]);
+      }
     }
     // nodal term of this plane at the thread's nodes: alpha (v - shift_j) X_j
     V nod[P];
@@ -471,26 +544,44 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       const int oy = jy * P + yi;
       const V xv = stg[((oy + 1) * RX + ox + 1) * NCP + cv];
       nod[yi] = vfmav(vrsub(alpha * vv[yi], ash), xv, vzero<V>());
+      // graded meshes: carried divided by D (restored at the output)
+      if constexpr (GR) nod[yi] = vmul((T)(sxy[yi] * p.m1[2][gz] * p.dn[2][gz]), nod[yi]);
     }
 
     // ---- z: accumulate the planes of the current z-cell
     const int n = gz / P, kz = gz - n * P;
+    // graded meshes: R, S of this plane scaled by the z-cell's scalars (the
+    // vertex plane belongs to two cells)
+    V Rz[P], Sz[P];
+    auto zscale = [&](int cell) {
+      if constexpr (GR) {
+        const int ec = min(cell, p.ncz - 1);
+        const T sb = (T)p.cB[2][ec], sa = (T)p.cA[2][ec];
+#pragma unroll
+        for (int yi = 0; yi < P; ++yi) {
+          Rz[yi] = vmul(sb, R[yi]);
+          Sz[yi] = vmul(sa, Sv[yi]);
+        }
+      }
+    };
+    const V *Ru = GR ? Rz : R, *Su = GR ? Sz : Sv;
     auto zall = [&](int k) {
 #pragma unroll
       for (int i = 0; i <= P; ++i) {
         const CT b = cf.Bz[i * (P + 1) + k], a = cf.Az[i * (P + 1) + k];
 #pragma unroll
-        for (int yi = 0; yi < P; ++yi) acc[i][yi] = vfma(b, R[yi], vfma(a, Sv[yi], acc[i][yi]));
+        for (int yi = 0; yi < P; ++yi) acc[i][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[i][yi]));
       }
     };
     auto zrow0 = [&](int k) {
       const CT b = cf.Bz[k], a = cf.Az[k];
 #pragma unroll
-      for (int yi = 0; yi < P; ++yi) acc[0][yi] = vfma(b, R[yi], vfma(a, Sv[yi], acc[0][yi]));
+      for (int yi = 0; yi < P; ++yi) acc[0][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[0][yi]));
     };
     if (gz <= gz_end) {
       if (kz == 0 && gz > n0 * P) {
         // vertex plane: close cell n-1, write its planes, carry the vertex
+        zscale(n - 1);
         zall(P);
 #pragma unroll
         for (int i = 0; i < P; ++i) {
@@ -503,11 +594,14 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
 #pragma unroll
           for (int i = 1; i <= P; ++i) acc[i][yi] = vzero<V>();
         }
+        zscale(n);
         if (gz < gz_end) zall(0);
         else if (extra) zrow0(0);
       } else if (kz == 0) {
+        zscale(n);
         zall(0);                      // bottom vertex of a segment: not owned here
       } else {
+        zscale(n);
         zall(kz);
 #pragma unroll
         for (int i = 1; i < P; ++i)
@@ -519,6 +613,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
     } else {
       // planes above the top vertex of the segment: row 0 of the next cell
       const int kk = gz - gz_end;
+      zscale(n1);
       zrow0(kk);
       if (kk == P) emit(gz_end, acc[0]);
     }
@@ -527,7 +622,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       const int s1 = (it + 1) % NST;
       if (!wait_parity(&full[s1], (uint32_t)(((it + 1) / NST) & 1))) abort_flag = 1;
       V *Pw = Px + ((it + 1) & 1) * 2 * RY * PXS;
-      xsweep(stage0 + s1 * S::STAGE_STRIDE_V, Pw, Pw + RY * PXS);
+      xsweep(stage0 + s1 * S::STAGE_STRIDE_V, Pw, Pw + RY * PXS, gz + 1);
     }
     __syncthreads();
     // the stage of plane it is free: fetch the plane NST ahead into it
@@ -590,9 +685,25 @@ void eo_blocks(const double *M, CT *e, CT *o) {
 }
 
 template <typename T, int VW, int P, typename CT>
-void make_coef(const Geom &g, double alpha, SweepCoef<CT, P> *cf) {
+void make_coef(const Geom &g, double alpha, bool graded, SweepCoef<CT, P> *cf) {
   constexpr int Q = P + 1;
   double Ah[Q * Q], Bh[Q * Q];
+  if (graded) {
+    // the reference blocks; D and the cell scalars are applied in the kernel
+    for (int i = 0; i < Q * Q; ++i) {
+      Ah[i] = g.A[i];
+      Bh[i] = g.B[i];
+    }
+    eo_blocks<P, T, VW>(Ah, cf->eAx, cf->oAx);
+    eo_blocks<P, T, VW>(Bh, cf->eBx, cf->oBx);
+    eo_blocks<P, T, VW>(Ah, cf->eAy, cf->oAy);
+    eo_blocks<P, T, VW>(Bh, cf->eBy, cf->oBy);
+    for (int i = 0; i < Q * Q; ++i) {
+      cf->Az[i] = CoefOf<T, VW>::make(0.5 * alpha * Ah[i]);
+      cf->Bz[i] = CoefOf<T, VW>::make(0.5 * alpha * Bh[i]);
+    }
+    return;
+  }
   scaled_blocks<P>(g, 0, Ah, Bh);
   eo_blocks<P, T, VW>(Ah, cf->eAx, cf->oAx);
   eo_blocks<P, T, VW>(Bh, cf->eBx, cf->oBx);
@@ -607,11 +718,11 @@ void make_coef(const Geom &g, double alpha, SweepCoef<CT, P> *cf) {
 }
 
 template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
-          bool HE>
+          bool HE, bool GR>
 cudaError_t run_sweep(const SweepArgs<T, typename CoefOf<T, VW>::type, P> &a, const CUtensorMap &tm,
                       int nitems, cudaStream_t s) {
   using Sh = SweepShape<T, P, C, TX, TY, XPT, VW>;
-  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, VW, HW, HE>;
+  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, VW, HW, HE, GR>;
   const size_t smem = Sh::smem(NST);
   cudaError_t e = raise_smem_limit(k, smem);
   if (e != cudaSuccess) return e;
@@ -622,13 +733,19 @@ cudaError_t run_sweep(const SweepArgs<T, typename CoefOf<T, VW>::type, P> &a, co
 
 // One tile variant: C columns per CTA, a TX x TY owned column of nodes, NST
 // planes in flight, XPT x-cells per x task, MINB CTAs per SM for the
-// register budget, VW columns per thread.
-template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW>
+// register budget, VW columns per thread; GR: the graded-mesh form.
+template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool GR>
 cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *err, int seglen,
                           cudaStream_t s) {
   using Sh = SweepShape<T, P, C, TX, TY, XPT, VW>;
   SweepArgs<T, typename CoefOf<T, VW>::type, P> sa;
-  make_coef<T, VW>(g, a.alpha, &sa.cf);
+  make_coef<T, VW>(g, a.alpha, GR, &sa.cf);
+  for (int ax = 0; ax < 3; ++ax) {
+    sa.dn[ax] = g.dnode[ax];
+    sa.m1[ax] = g.m1node[ax];
+    sa.cA[ax] = g.cellA[ax];
+    sa.cB[ax] = g.cellB[ax];
+  }
   sa.Z = a.Z;
   sa.W = a.W;
   sa.E = a.E;
@@ -640,13 +757,17 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   sa.beta = a.beta;
   sa.err = err;
   sa.ncol = a.ncol;
-  sa.nx = sa.ny = sa.nz = g.Ni;
-  sa.ncz = g.ncell;
-  sa.ntx = (g.Ni + TX - 1) / TX;
-  sa.nty = (g.Ni + TY - 1) / TY;
+  sa.nx = g.n[0];
+  sa.ny = g.n[1];
+  sa.nz = g.n[2];
+  sa.ncx = g.nc[0];
+  sa.ncy = g.nc[1];
+  sa.ncz = g.nc[2];
+  sa.ntx = (g.n[0] + TX - 1) / TX;
+  sa.nty = (g.n[1] + TY - 1) / TY;
   sa.nchunk = (a.ncol + C - 1) / C;
-  sa.seglen = std::max(1, std::min(seglen, g.ncell));
-  const int nseg = (g.ncell + sa.seglen - 1) / sa.seglen;
+  sa.seglen = std::max(1, std::min(seglen, g.nc[2]));
+  const int nseg = (g.nc[2] + sa.seglen - 1) / sa.seglen;
   const long long nitems = (long long)sa.ntx * sa.nty * sa.nchunk * nseg;
   if (nitems > 0x7fffffffLL) return cudaErrorInvalidValue;
   // X as a 4D tensor (column, x, y, z) of the unknown grid; box = one plane
@@ -654,10 +775,10 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tm;
-  const cuuint64_t dims[4] = {(cuuint64_t)a.ncol, (cuuint64_t)g.Ni, (cuuint64_t)g.Ni,
-                              (cuuint64_t)g.Ni};
+  const cuuint64_t dims[4] = {(cuuint64_t)a.ncol, (cuuint64_t)g.n[0], (cuuint64_t)g.n[1],
+                              (cuuint64_t)g.n[2]};
   const cuuint64_t row = (cuuint64_t)a.ncol * sizeof(T);
-  const cuuint64_t strides[3] = {row, row * g.Ni, row * g.Ni * g.Ni};
+  const cuuint64_t strides[3] = {row, row * g.n[0], row * g.n[0] * g.n[1]};
   const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)Sh::RX, (cuuint32_t)Sh::RY, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(&tm, sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -668,43 +789,53 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   const bool hw = a.W != nullptr, he = a.E != nullptr;
   const int n = (int)nitems;
   if constexpr (std::is_same<T, float>::value) {
-    if (hw && he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, true>(sa, tm, n, s);
-    if (he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, true>(sa, tm, n, s);
+    if (hw && he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, true, GR>(sa, tm, n, s);
+    if (he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, true, GR>(sa, tm, n, s);
   } else {
     if (he) return cudaErrorInvalidValue;
   }
-  if (hw) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, false>(sa, tm, n, s);
-  return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, false>(sa, tm, n, s);
+  if (hw) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, false, GR>(sa, tm, n, s);
+  return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, false, GR>(sa, tm, n, s);
 }
 
 using SweepFn32 = cudaError_t (*)(const Geom &, const float *, const HxArgs<float> &, int *, int,
                                   cudaStream_t);
 using SweepFn64 = cudaError_t (*)(const Geom &, const double *, const HxArgs<double> &, int *,
                                   int, cudaStream_t);
-// Tile variants per (precision, order), the first one the default.
+// Tile variants per (precision, order, mesh kind), the first one the default.
+// Meshes of equal cells per axis (cubes or boxes of box cells) fold D and the
+// cell size into the coefficients; graded meshes take the GR form.
 const SweepFn32 kVar32q4[] = {
-    sweep_variant<float, 4, 8, 16, 16, 4, 2, 2, 2>,   // 256 threads, two CTAs per SM
-    sweep_variant<float, 4, 16, 16, 16, 3, 1, 1, 2>,  // 512 threads, one x-cell per x task
-    sweep_variant<float, 4, 16, 16, 16, 4, 2, 1, 2>,  // 512 threads, four planes in flight
-    sweep_variant<float, 4, 8, 16, 32, 4, 2, 1, 2>,   // 512 threads, taller tile (less halo)
+    sweep_variant<float, 4, 8, 16, 16, 4, 2, 2, 2, false>,   // 256 threads, two CTAs per SM
+    sweep_variant<float, 4, 16, 16, 16, 3, 1, 1, 2, false>,  // 512 threads, one x-cell per task
+    sweep_variant<float, 4, 16, 16, 16, 4, 2, 1, 2, false>,  // 512 threads, four planes in flight
+    sweep_variant<float, 4, 8, 16, 32, 4, 2, 1, 2, false>,   // 512 threads, taller tile (less halo)
 };
 // (one column per thread in FP32 -- scalar FMAs instead of packed pairs -- was
 // measured at 0.81 to 1.18 ms against 0.51 ms on the 32^3 x 64 case, and is not
 // offered)
-const SweepFn32 kVar32q2[] = {sweep_variant<float, 2, 16, 16, 8, 3, 2, 1, 2>};
+const SweepFn32 kVar32q2[] = {sweep_variant<float, 2, 16, 16, 8, 3, 2, 1, 2, false>};
+const SweepFn32 kVar32q6[] = {sweep_variant<float, 6, 16, 12, 12, 3, 2, 1, 2, false>};
+const SweepFn32 kVar32q4g[] = {sweep_variant<float, 4, 8, 16, 16, 4, 2, 2, 2, true>};
+const SweepFn32 kVar32q2g[] = {sweep_variant<float, 2, 16, 16, 8, 3, 2, 1, 2, true>};
+const SweepFn32 kVar32q6g[] = {sweep_variant<float, 6, 16, 12, 12, 3, 2, 1, 2, true>};
 const SweepFn64 kVar64q4[] = {
-    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 1>,  // one column per thread, 512 threads
-    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 2>,  // column pairs, 256 threads
-    sweep_variant<double, 4, 8, 16, 16, 3, 1, 1, 2>,
+    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 1, false>,  // one column per thread, 512 threads
+    sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 2, false>,  // column pairs, 256 threads
+    sweep_variant<double, 4, 8, 16, 16, 3, 1, 1, 2, false>,
 };
-const SweepFn64 kVar64q2[] = {sweep_variant<double, 2, 8, 16, 8, 3, 2, 1, 2>};
+const SweepFn64 kVar64q2[] = {sweep_variant<double, 2, 8, 16, 8, 3, 2, 1, 2, false>};
+const SweepFn64 kVar64q6[] = {sweep_variant<double, 6, 8, 12, 12, 3, 2, 1, 1, false>};
+const SweepFn64 kVar64q4g[] = {sweep_variant<double, 4, 8, 16, 16, 3, 2, 1, 1, true>};
+const SweepFn64 kVar64q2g[] = {sweep_variant<double, 2, 8, 16, 8, 3, 2, 1, 2, true>};
+const SweepFn64 kVar64q6g[] = {sweep_variant<double, 6, 8, 12, 12, 3, 2, 1, 1, true>};
 template <typename A, size_t N> constexpr int count_of(const A (&)[N]) { return (int)N; }
 
 }  // namespace
 
 bool sweep_supported(const Geom &g, int ncol, size_t elem, const void *X, const void *Z,
                      const void *W, const void *E) {
-  if (!(g.p == 2 || g.p == 4)) return false;
+  if (!(g.p == 2 || g.p == 4 || g.p == 6)) return false;
   if (ncol < 2 || ncol > kMaxCols || (ncol * elem) % 16 != 0) return false;
   if (((uintptr_t)X & 15) != 0 || ((uintptr_t)Z & 15) != 0) return false;
   if (W && ((uintptr_t)W & 15) != 0) return false;
@@ -713,23 +844,42 @@ bool sweep_supported(const Geom &g, int ncol, size_t elem, const void *X, const 
   return Z != X && Z != W && Z != E;
 }
 
+namespace {
+template <typename Fn, size_t A, size_t B, size_t C2, size_t D, size_t E2, size_t F>
+std::pair<const Fn *, int> pick(const Geom &g, const Fn (&q2)[A], const Fn (&q4)[B],
+                                const Fn (&q6)[C2], const Fn (&q2g)[D], const Fn (&q4g)[E2],
+                                const Fn (&q6g)[F]) {
+  if (g.graded) {
+    if (g.p == 2) return {q2g, (int)D};
+    if (g.p == 4) return {q4g, (int)E2};
+    return {q6g, (int)F};
+  }
+  if (g.p == 2) return {q2, (int)A};
+  if (g.p == 4) return {q4, (int)B};
+  return {q6, (int)C2};
+}
+}  // namespace
+
 int sweep_variants(const Geom &g, size_t elem) {
-  if (elem == 4) return g.p == 4 ? count_of(kVar32q4) : count_of(kVar32q2);
-  return g.p == 4 ? count_of(kVar64q4) : count_of(kVar64q2);
+  if (elem == 4)
+    return pick<SweepFn32>(g, kVar32q2, kVar32q4, kVar32q6, kVar32q2g, kVar32q4g, kVar32q6g).second;
+  return pick<SweepFn64>(g, kVar64q2, kVar64q4, kVar64q6, kVar64q2g, kVar64q4g, kVar64q6g).second;
 }
 
 cudaError_t launch_hx_sweep(const Geom &g, const float *v, const HxArgs<float> &a, int *err,
                             int variant, int seglen, cudaStream_t s) {
   if (!sweep_supported(g, a.ncol, sizeof(float), a.X, a.Z, a.W, a.E)) return cudaErrorInvalidValue;
-  if (variant < 0 || variant >= sweep_variants(g, 4)) return cudaErrorInvalidValue;
-  return (g.p == 4 ? kVar32q4 : kVar32q2)[variant](g, v, a, err, seglen, s);
+  auto t = pick<SweepFn32>(g, kVar32q2, kVar32q4, kVar32q6, kVar32q2g, kVar32q4g, kVar32q6g);
+  if (variant < 0 || variant >= t.second) return cudaErrorInvalidValue;
+  return t.first[variant](g, v, a, err, seglen, s);
 }
 cudaError_t launch_hx_sweep(const Geom &g, const double *v, const HxArgs<double> &a, int *err,
                             int variant, int seglen, cudaStream_t s) {
   if (!sweep_supported(g, a.ncol, sizeof(double), a.X, a.Z, a.W, nullptr) || a.E)
     return cudaErrorInvalidValue;
-  if (variant < 0 || variant >= sweep_variants(g, 8)) return cudaErrorInvalidValue;
-  return (g.p == 4 ? kVar64q4 : kVar64q2)[variant](g, v, a, err, seglen, s);
+  auto t = pick<SweepFn64>(g, kVar64q2, kVar64q4, kVar64q6, kVar64q2g, kVar64q4g, kVar64q6g);
+  if (variant < 0 || variant >= t.second) return cudaErrorInvalidValue;
+  return t.first[variant](g, v, a, err, seglen, s);
 }
 
 }  // namespace invdft

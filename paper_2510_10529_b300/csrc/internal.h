@@ -13,7 +13,7 @@
 
 namespace invdft {
 
-constexpr int kMaxOrder = 4;
+constexpr int kMaxOrder = 6;
 constexpr int kMaxQ = kMaxOrder + 1;
 constexpr int kMaxCols = 256;       // widest block H~X accepts
 constexpr int kMaxGram = 128;       // widest block of Gram / rotation work
@@ -29,33 +29,50 @@ constexpr int kStWaitGram = 10;     // deflation Gram on the tensor cores
 constexpr int kStWaitCount = 3;
 
 // Geometry and 1D factors of the cell operator, passed to kernels by value.
-// K_e = kc * (B (x) B (x) A + B (x) A (x) B + A (x) B (x) B)  (z, y, x order),
-// kc = h/4, with A, B the 1D GLL stiffness and consistent mass on [-1, 1].
+// A cell is a box with sizes (h_x, h_y, h_z); with A, B the 1D GLL stiffness
+// and consistent mass on [-1, 1] and per-axis A_a = (2/h_a) A, B_a = (h_a/2) B,
+//   K_e = 1/2 (B_z (x) B_y (x) A_x + B_z (x) A_y (x) B_x + A_z (x) B_y (x) B_x);
+// on a uniform cube this is kc (B (x) B (x) A + ...) with kc = h/4.
 struct Geom {
-  int p, q, ncell, Ni;      // order, nodes per cell edge, cells per axis, unknowns per axis
+  int p, q;                 // order, nodes per cell edge
+  int nc[3], n[3];          // cells and unknowns per axis (x, y, z)
+  int ncell, Ni;            // nc[0], n[0]: the cube-only kernels (tensor cores, batch)
+  bool cube;                // equal cells, the same on every axis
+  bool graded;              // some axis has unequal cells
   long long L;              // unknowns
-  double kc;
+  double kc;                // h/4 on a cube
   double A[kMaxQ * kMaxQ];
   double B[kMaxQ * kMaxQ];
-  // per axis (x, y, z): half the cell size s = h/2, and d = m1^-1/2 at the
-  // local nodes of a cell away from the boundary (an interior vertex has
-  // m1 = 2 s w_0, node i in between m1 = s w_i)
+  // per axis (x, y, z), for axes of equal cells: half the cell size s = h/2,
+  // and d = m1^-1/2 at the local nodes of a cell away from the boundary (an
+  // interior vertex has m1 = 2 s w_0, node i in between m1 = s w_i)
   double s[3];
   double dl[3][kMaxQ];
-  const double *dm1;        // device [Ni + 2]: 1/sqrt(m1) along one axis (0 at the ends)
+  // device tables per axis: d = m1^-1/2 at every node of the axis (0 at the two
+  // boundary nodes), the cell scalars 2/h_e and h_e/2, the node coordinates
+  const double *dnode[3] = {}, *m1node[3] = {}, *cellA[3] = {}, *cellB[3] = {}, *axis[3] = {};
+  const double *dm1;        // dnode[0] (cube kernels)
   const float *dm1f;        // the same table in FP32 (tensor-core path)
 };
 
-// Host-side FE tables (tables.cu).
+// Host-side FE tables (tables.cu): per axis, the cell breaks and sizes, the
+// node coordinates, the 1D lumped mass and the assembled 1D matrix diagonals,
+// all over the axis's nodes including the two boundary nodes.
+struct AxisTab {
+  std::vector<double> breaks, h;      // ncell + 1, ncell
+  std::vector<double> axis;           // node coordinates, ncell p + 1
+  std::vector<double> m1;             // 1D lumped mass
+  std::vector<double> kdiag1_A, kdiag1_B;  // assembled 1D diagonals (for the preconditioner)
+  bool uniform = true;                // equal cells
+};
 struct Tables {
   std::vector<double> gll_x, gll_w;   // q
   std::vector<double> A, B;           // q x q
   std::vector<double> Dm;             // q x q: l_j'(x_i) at the GLL nodes on [-1, 1]
-  std::vector<double> axis;           // node coordinates along one axis, Ni + 2
-  std::vector<double> m1;             // 1D lumped mass, Ni + 2
-  std::vector<double> kdiag1_A, kdiag1_B;  // assembled 1D diagonals (for the preconditioner)
+  AxisTab ax[3];                      // x, y, z
 };
-void build_tables(double lo, double hi, int ncell, int p, Tables *t);
+void build_reference(int p, Tables *t);
+void build_axis(const Tables &ref, const std::vector<double> &breaks, int p, AxisTab *ax);
 
 // Bump allocator over the caller's workspace.
 struct Arena {
@@ -117,9 +134,10 @@ struct Ctx {
   bool have_upper = false;
 
   // ---- device state (inside the workspace)
-  double *dm1 = nullptr;            // [Ni+2]
-  float *dm1f = nullptr;            // [Ni+2] FP32 copy
-  double *m1tab = nullptr, *kAtab = nullptr, *kBtab = nullptr;  // [Ni+2] 1D tables
+  double *dnode[3] = {};            // [n_a + 2] per axis: m1^-1/2 (0 at the boundary)
+  float *dm1f = nullptr;            // [n_x + 2] FP32 copy of dnode[0] (cube kernels)
+  double *m1tab[3] = {}, *kAtab[3] = {}, *kBtab[3] = {};  // [n_a + 2] 1D tables per axis
+  double *cellA[3] = {}, *cellB[3] = {}, *axis[3] = {};    // per axis: 2/h_e, h_e/2; coordinates
   double *mass = nullptr;           // [L]
   double *dvec = nullptr;           // [L]  m^-1/2
   double *prec_diag = nullptr;      // [L]  1 / diag(D K D)

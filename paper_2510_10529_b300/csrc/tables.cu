@@ -71,7 +71,7 @@ void gauss(int n, std::vector<double> *x, std::vector<double> *w) {
 
 }  // namespace
 
-void build_tables(double lo, double hi, int ncell, int p, Tables *t) {
+void build_reference(int p, Tables *t) {
   const int q = p + 1;
   gll(p, &t->gll_x, &t->gll_w);
   const std::vector<double> &xn = t->gll_x;
@@ -124,23 +124,34 @@ void build_tables(double lo, double hi, int ncell, int p, Tables *t) {
       t->A[i * q + j] = a;
       t->B[i * q + j] = b;
     }
-  // axis coordinates and 1D assembled lumped mass / matrix diagonals
+}
+
+void build_axis(const Tables &ref, const std::vector<double> &breaks, int p, AxisTab *ax) {
+  const int q = p + 1;
+  const int ncell = (int)breaks.size() - 1;
   const int N = ncell * p + 1;
-  const double h = (hi - lo) / ncell, s = 0.5 * h;
-  t->axis.assign(N, 0.0);
-  t->m1.assign(N, 0.0);
-  t->kdiag1_A.assign(N, 0.0);
-  t->kdiag1_B.assign(N, 0.0);
-  for (int e = 0; e < ncell; ++e)
+  ax->breaks = breaks;
+  ax->h.assign(ncell, 0.0);
+  ax->axis.assign(N, 0.0);
+  ax->m1.assign(N, 0.0);
+  ax->kdiag1_A.assign(N, 0.0);
+  ax->kdiag1_B.assign(N, 0.0);
+  ax->uniform = true;
+  const double h0 = (breaks[ncell] - breaks[0]) / ncell;
+  for (int e = 0; e < ncell; ++e) {
+    const double h = breaks[e + 1] - breaks[e], s = 0.5 * h;
+    ax->h[e] = h;
+    if (std::fabs(h - h0) > 1e-12 * std::fabs(h0)) ax->uniform = false;
     for (int i = 0; i < q; ++i) {
-      int gi = e * p + i;
-      t->axis[gi] = lo + e * h + s * (xn[i] + 1.0);
-      t->m1[gi] += s * t->gll_w[i];
-      t->kdiag1_A[gi] += t->A[i * q + i] / s;
-      t->kdiag1_B[gi] += t->B[i * q + i] * s;
+      const int gi = e * p + i;
+      ax->axis[gi] = breaks[e] + s * (ref.gll_x[i] + 1.0);
+      ax->m1[gi] += s * ref.gll_w[i];
+      ax->kdiag1_A[gi] += ref.A[i * q + i] / s;
+      ax->kdiag1_B[gi] += ref.B[i * q + i] * s;
     }
-  t->axis[0] = lo;
-  t->axis[N - 1] = hi;
+  }
+  ax->axis[0] = breaks[0];
+  ax->axis[N - 1] = breaks[ncell];
 }
 
 }  // namespace invdft

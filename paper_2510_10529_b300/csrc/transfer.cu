@@ -1,6 +1,6 @@
 // Linear (Q1) v_xc mesh and the field transfer to and from the orbital mesh
 // (Sec. 3.1.1, Sec. 3.2.2).  The Q1 mesh is a uniform mesh of nv cells per axis
-// over the orbital mesh's box, with v_xc on all of its (nv+1)^3 nodes (x
+// over the orbital mesh's box (equal or graded orbital cells), with v_xc on all of its (nv+1)^3 nodes (x
 // fastest).  The transfer matrix T holds the trilinear weights of the Q1
 // interpolant at the orbital mesh's unknown nodes (8 per node):
 //   v_nodes = T v_q1                 (v_xc seen by the orbitals),
@@ -19,23 +19,18 @@ namespace invdft {
 namespace {
 
 struct AxisGeom {
-  int ncell, p;            // orbital cells and order along the axis (uniform cells)
-  double lo, h;            // box start and cell size
-  double xi[kMaxQ];        // GLL points on [-1, 1]
+  const double *x;         // orbital node coordinates along the axis, boundary included
+  int nnodes;              // n + 2
 };
 struct TransferGeom {
   AxisGeom ax[3];
   int n[3];                // orbital unknowns per axis
   int nv;                  // Q1 cells per axis
-  double vlo, hv;          // Q1 box start and cell size
+  double vlo[3], hv[3];    // Q1 box start and cell size per axis
 };
 
-// coordinate of orbital node g (0 .. ncell p, the boundary included)
-__device__ __forceinline__ double node_x(const AxisGeom &A, int g) {
-  if (g >= A.ncell * A.p) return A.lo + A.ncell * A.h;
-  const int e = g / A.p, l = g - e * A.p;
-  return A.lo + e * A.h + 0.5 * A.h * (A.xi[l] + 1.0);
-}
+// coordinate of orbital node g (0 .. n + 1, the boundary included)
+__device__ __forceinline__ double node_x(const AxisGeom &A, int g) { return A.x[g]; }
 
 __global__ void q1_to_nodes_kernel(TransferGeom G, const double *__restrict__ vq,
                                    double *__restrict__ out) {
@@ -48,7 +43,7 @@ __global__ void q1_to_nodes_kernel(TransferGeom G, const double *__restrict__ vq
     int c[3];
     double f[3];
     for (int d = 0; d < 3; ++d) {
-      const double t = (node_x(G.ax[d], u[d] + 1) - G.vlo) / G.hv;
+      const double t = (node_x(G.ax[d], u[d] + 1) - G.vlo[d]) / G.hv[d];
       int ci = (int)floor(t);
       ci = ci < 0 ? 0 : (ci > G.nv - 1 ? G.nv - 1 : ci);
       c[d] = ci;
@@ -67,13 +62,18 @@ __global__ void q1_to_nodes_kernel(TransferGeom G, const double *__restrict__ vq
 }
 
 // orbital unknowns (0-based) whose coordinate lies within one Q1 cell of X:
-// [*first, *last]; the hat weight is zero outside
+// [*first, *last]; the hat weight is zero outside.  The node coordinates
+// increase, so the first node right of X - hv is found by bisection.
 __device__ __forceinline__ void support(const AxisGeom &A, int n, double X, double hv, int *first,
                                         int *last) {
-  int e = (int)floor((X - hv - A.lo) / A.h);
-  e = e < 0 ? 0 : (e > A.ncell - 1 ? A.ncell - 1 : e);
-  int g = e * A.p;
-  while (g <= n && node_x(A, g) <= X - hv) ++g;
+  int lo = 0, hi = n + 1;               // x[lo] <= X - hv < x[hi] unless at the ends
+  if (node_x(A, 0) > X - hv) hi = 0;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (node_x(A, mid) <= X - hv) lo = mid;
+    else hi = mid;
+  }
+  int g = hi;
   int g1 = g;
   while (g1 + 1 <= n && node_x(A, g1 + 1) < X + hv) ++g1;
   *first = (g < 1 ? 1 : g) - 1;
@@ -90,19 +90,19 @@ __global__ void nodes_to_q1_kernel(TransferGeom G, const double *__restrict__ g,
     int lo[3], hi[3];
     double X[3];
     for (int d = 0; d < 3; ++d) {
-      X[d] = G.vlo + bi[d] * G.hv;
-      support(G.ax[d], G.n[d], X[d], G.hv, &lo[d], &hi[d]);
+      X[d] = G.vlo[d] + bi[d] * G.hv[d];
+      support(G.ax[d], G.n[d], X[d], G.hv[d], &lo[d], &hi[d]);
     }
     double s = 0.0;
     for (int uz = lo[2]; uz <= hi[2]; ++uz) {
-      const double wz = fmax(0.0, 1.0 - fabs(node_x(G.ax[2], uz + 1) - X[2]) / G.hv);
+      const double wz = fmax(0.0, 1.0 - fabs(node_x(G.ax[2], uz + 1) - X[2]) / G.hv[2]);
       double sy = 0.0;
       for (int uy = lo[1]; uy <= hi[1]; ++uy) {
-        const double wy = fmax(0.0, 1.0 - fabs(node_x(G.ax[1], uy + 1) - X[1]) / G.hv);
+        const double wy = fmax(0.0, 1.0 - fabs(node_x(G.ax[1], uy + 1) - X[1]) / G.hv[1]);
         const double *row = g + (long long)G.n[0] * (uy + (long long)G.n[1] * uz);
         double sx = 0.0;
         for (int ux = lo[0]; ux <= hi[0]; ++ux) {
-          const double wx = fmax(0.0, 1.0 - fabs(node_x(G.ax[0], ux + 1) - X[0]) / G.hv);
+          const double wx = fmax(0.0, 1.0 - fabs(node_x(G.ax[0], ux + 1) - X[0]) / G.hv[0]);
           sx += wx * row[ux];
         }
         sy += wy * sx;
@@ -115,18 +115,15 @@ __global__ void nodes_to_q1_kernel(TransferGeom G, const double *__restrict__ g,
 
 bool make_geom(invdft_handle h, int nv, TransferGeom *G) {
   if (nv < 1 || nv > 4096) return false;
+  if (!h->bound) return false;
   for (int d = 0; d < 3; ++d) {
-    AxisGeom &A = G->ax[d];
-    A.ncell = h->g.ncell;
-    A.p = h->g.p;
-    A.lo = h->mesh.lo;
-    A.h = 2.0 * h->g.s[d];
-    for (int i = 0; i <= A.p; ++i) A.xi[i] = h->tab.gll_x[i];
-    G->n[d] = h->g.Ni;
+    G->ax[d].x = h->g.axis[d];
+    G->ax[d].nnodes = h->g.n[d] + 2;
+    G->n[d] = h->g.n[d];
+    G->vlo[d] = h->mesh.lo[d];
+    G->hv[d] = (h->mesh.hi[d] - h->mesh.lo[d]) / nv;
   }
   G->nv = nv;
-  G->vlo = h->mesh.lo;
-  G->hv = (h->mesh.hi - h->mesh.lo) / nv;
   return true;
 }
 
@@ -139,7 +136,7 @@ extern "C" invdft_status invdft_q1_to_nodes(invdft_handle h, int nv, const doubl
                                             double *v_nodes, void *stream) {
   TransferGeom G;
   if (!h || !v_q1 || !v_nodes || !make_geom(h, nv, &G)) {
-    if (h) h->err = "q1_to_nodes: bad arguments (nv in [1, 4096], device arrays)";
+    if (h) h->err = "q1_to_nodes: bad arguments (bound handle, nv in [1, 4096], device arrays)";
     return INVDFT_EINVAL;
   }
   const long long L = h->L;
@@ -154,7 +151,7 @@ extern "C" invdft_status invdft_grad_to_q1(invdft_handle h, int nv, const double
                                            double *g_q1, void *stream) {
   TransferGeom G;
   if (!h || !g_nodes || !g_q1 || !make_geom(h, nv, &G)) {
-    if (h) h->err = "grad_to_q1: bad arguments (nv in [1, 4096], device arrays)";
+    if (h) h->err = "grad_to_q1: bad arguments (bound handle, nv in [1, 4096], device arrays)";
     return INVDFT_EINVAL;
   }
   const long long NQ = (long long)(nv + 1) * (nv + 1) * (nv + 1);

@@ -38,7 +38,7 @@ def test_library_exports_every_declared_symbol():
 def test_node_coordinates_match_oracle(ncell, order):
     import paper_2510_10529_b300 as P
     from oracle import fe
-    mesh = P.MeshDesc(lo=-8.0, hi=8.0, ncell=ncell, order=order)
+    mesh = P.MeshDesc.make(-8.0, 8.0, ncell, order)
     opts = P.Opts(nstates=4, n_electrons=2.0)
     h, L = P.invdft_create_mesh(mesh, opts)
     try:
@@ -51,14 +51,47 @@ def test_node_coordinates_match_oracle(ncell, order):
         P.invdft_destroy(h)
 
 
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_graded_box_node_coordinates_match_oracle(order):
+    """A box with different extents and cell counts per axis, cells graded
+    towards two points on x and equal on y and z (invdft_mesh_desc with
+    per-axis breaks), against the graded-mesh oracle's nodes."""
+    import paper_2510_10529_b300 as P
+    from oracle import graded
+    bx = graded.graded_breaks(-6.0, 5.0, 5, [-1.0, 2.0], 0.6, 3.0)
+    by = np.linspace(-4.0, 4.0, 4)
+    bz = np.linspace(-3.0, 5.0, 3)
+    mesh = P.MeshDesc.make([-6.0, -4.0, -3.0], [5.0, 4.0, 5.0], [5, 3, 2], order,
+                           breaks=[bx, None, bz])
+    h, L = P.invdft_create_mesh(mesh, P.Opts(nstates=2, n_electrons=2.0))
+    try:
+        om = graded.GradedMesh(bx, by, bz, order)
+        assert L == om.L
+        np.testing.assert_allclose(P.invdft_node_coords(h, L), om.coords(), atol=1e-13)
+    finally:
+        P.invdft_destroy(h)
+
+
+def test_create_rejects_bad_breaks():
+    import paper_2510_10529_b300 as P
+    bad = [np.array([0.0, 0.6, 0.5, 1.0]), None, None]      # not increasing
+    with pytest.raises(P.InvdftError):
+        P.invdft_create_mesh(P.MeshDesc.make(0.0, 1.0, [3, 2, 2], 2, breaks=bad),
+                             P.Opts(nstates=2))
+    off = [np.array([0.1, 0.5, 1.0]), None, None]            # does not start at lo
+    with pytest.raises(P.InvdftError):
+        P.invdft_create_mesh(P.MeshDesc.make(0.0, 1.0, [2, 2, 2], 2, breaks=off),
+                             P.Opts(nstates=2))
+
+
 def test_create_rejects_bad_arguments():
     import paper_2510_10529_b300 as P
     with pytest.raises(P.InvdftError):
-        P.invdft_create_mesh(P.MeshDesc(lo=0.0, hi=1.0, ncell=2, order=3), P.Opts(nstates=2))
+        P.invdft_create_mesh(P.MeshDesc.make(0.0, 1.0, 2, 3), P.Opts(nstates=2))
     with pytest.raises(P.InvdftError):
-        P.invdft_create_mesh(P.MeshDesc(lo=0.0, hi=1.0, ncell=2, order=2), P.Opts(nstates=0))
+        P.invdft_create_mesh(P.MeshDesc.make(0.0, 1.0, 2, 2), P.Opts(nstates=0))
     with pytest.raises(P.InvdftError):
-        P.invdft_create_mesh(P.MeshDesc(lo=1.0, hi=0.0, ncell=2, order=2), P.Opts(nstates=2))
+        P.invdft_create_mesh(P.MeshDesc.make(1.0, 0.0, 2, 2), P.Opts(nstates=2))
 
 
 def test_device_calls_validate_on_the_host_first():
@@ -68,7 +101,7 @@ def test_device_calls_validate_on_the_host_first():
     without a GPU.  The non-null pointers below are never dereferenced."""
     import paper_2510_10529_b300 as P
     from paper_2510_10529_b300._lib import INVDFT_EINVAL, INVDFT_ENOMEM, lib
-    h, L = P.invdft_create_mesh(P.MeshDesc(lo=-4.0, hi=4.0, ncell=2, order=2),
+    h, L = P.invdft_create_mesh(P.MeshDesc.make(-4.0, 4.0, 2, 2),
                                 P.Opts(nstates=2, n_electrons=2.0))
     fake = C.c_void_p(0x1000)
     st = P.Stats()
@@ -90,6 +123,10 @@ def test_device_calls_validate_on_the_host_first():
             "loss_grad": lambda: lib.invdft_loss_grad(h, fake, fake, C.byref(loss), fake,
                                                       C.byref(st), None),
             "step": lambda: lib.invdft_step(h, fake, fake, fake, C.byref(st), None),
+            "initial_guess": lambda: lib.invdft_initial_guess(h, fake, fake, 1e-2, 1.0, 1, fake,
+                                                              None),
+            "q1_to_nodes": lambda: lib.invdft_q1_to_nodes(h, 4, fake, fake, None),
+            "grad_to_q1": lambda: lib.invdft_grad_to_q1(h, 4, fake, fake, None),
         }
         for name, call in calls.items():
             code = call()
