@@ -344,6 +344,29 @@ invdft_status invdft_initial_guess(invdft_handle h, const double *rho_data, cons
                                    double tau, double alpha, int exchange, double *v_out,
                                    void *stream);
 
+/* Dense per-cell potential matrices: the Gauss-quadrature reading of the
+ * potential term of Eq. 17, V_e[a][b] = sum_g W_g v(x_g) N_a(x_g) N_b(x_g)
+ * with 2p Gauss points per axis (exact for the interpolated v), and the
+ * operator H~ = D (K + V) D with the lumped GLL mass (orders 2 and 4).
+ * invdft_cell_potential_bytes: bytes of the cell-matrix buffer for prec
+ *   (FP64: (p+1)^6 doubles per cell, row-major; MIXED: one 128 x 128 FP32
+ *   tile per cell in the tensor-core operand layout).
+ * invdft_cell_potentials: builds V_e of every cell into Ve (device, caller
+ *   owned, the size above) from v_full, the potential on the FULL node grid
+ *   including the Dirichlet boundary nodes (device, prod_a (ncell[a] p + 1)
+ *   doubles, x fastest).
+ * invdft_apply_h_dense: Y = D (K + V) D X for an [L][ncol] block (device;
+ *   double for FP64, float for MIXED; Y must not alias X, ncol in [1, 256]):
+ *   the kinetic part as in invdft_apply_h without the collocated potential,
+ *   then each cell's dense product added in.  The potential set by
+ *   invdft_set_potential is not used.
+ * EINVAL for bad arguments, an unbound handle or another order.            */
+invdft_status invdft_cell_potential_bytes(invdft_handle h, invdft_precision prec, size_t *bytes);
+invdft_status invdft_cell_potentials(invdft_handle h, const double *v_full, void *Ve,
+                                     invdft_precision prec, void *stream);
+invdft_status invdft_apply_h_dense(invdft_handle h, const void *Ve, const void *X, void *Y,
+                                   int ncol, invdft_precision prec, void *stream);
+
 /* Linear (Q1) v_xc mesh and field transfer (Sec. 3.1.1, Sec. 3.2.2).  The Q1
  * mesh has nv cells per axis (nv in [1, 4096]) over the handle's box, with
  * values on all (nv+1)^3 nodes (x fastest); T is the matrix of trilinear

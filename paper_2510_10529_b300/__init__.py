@@ -298,6 +298,28 @@ class Problem:
             self.h, False)
         return v
 
+    def cell_potentials(self, v_full, prec: str = "fp64"):
+        """Dense per-cell potential matrices (Gauss quadrature of Eq. 17) from v
+        on the full node grid (boundary included); returns the device buffer."""
+        pr = INVDFT_FP64 if prec == "fp64" else INVDFT_MIXED
+        n = C.c_size_t()
+        _ok("invdft_cell_potential_bytes",
+            lib.invdft_cell_potential_bytes(self.h, pr, C.byref(n)), self.h, False)
+        Ve = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        _ok("invdft_cell_potentials",
+            lib.invdft_cell_potentials(self.h, _ptr(v_full), _ptr(Ve), pr, _stream()),
+            self.h, False)
+        return Ve
+
+    def apply_h_dense(self, Ve, X):
+        """Y = D (K + V) D X with the dense cell potentials (X double or float)."""
+        Y = torch.empty_like(X)
+        pr = INVDFT_FP64 if X.dtype == torch.float64 else INVDFT_MIXED
+        _ok("invdft_apply_h_dense",
+            lib.invdft_apply_h_dense(self.h, _ptr(Ve), _ptr(X), _ptr(Y), X.shape[1], pr,
+                                     _stream()), self.h, False)
+        return Y
+
     def q1_to_nodes(self, nv: int, v_q1):
         """v_xc at the unknown nodes from a Q1 field of nv^3 cells (trilinear)."""
         v = self.zeros(self.L)

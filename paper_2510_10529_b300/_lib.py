@@ -102,6 +102,9 @@ def _load():
         "invdft_reset": [H],
         "invdft_initial_guess": [H, P, P, C.c_double, C.c_double, C.c_int, P, P],
         "invdft_q1_to_nodes": [H, C.c_int, P, P, P],
+        "invdft_cell_potential_bytes": [H, C.c_int, C.POINTER(C.c_size_t)],
+        "invdft_cell_potentials": [H, P, P, C.c_int, P],
+        "invdft_apply_h_dense": [H, P, P, P, C.c_int, C.c_int, P],
         "invdft_grad_to_q1": [H, C.c_int, P, P, P],
         "invdft_profile_hx": [H, C.c_int, P],
         "invdft_tune_hx": [H, C.c_int, C.c_int, P],

@@ -28,7 +28,7 @@ __global__ void hx_nodal(const T *__restrict__ X, T *__restrict__ Z, const doubl
     const uint32_t a = fdiv(i, fd);
     const int j = (int)(i - a * (uint32_t)ncol);
     const double sh = shift_col ? shift_col[j] : shift;
-    double z = alpha * (v[a] - sh) * (double)X[i];
+    double z = alpha * ((v ? v[a] : 0.0) - sh) * (double)X[i];
     if (W) z += beta * (double)W[i];
     if (E) z += alpha * escale[j] * (double)E[i];
     Z[i] = (T)z;
@@ -443,6 +443,25 @@ cudaError_t prof_flush(Ctx *c) {
 }
 
 cudaError_t hx_op(Ctx *c, const HxArgs<double> &a, cudaStream_t s) { return hx_op_t(c, a, s); }
+
+// D K D X (+ the shift, W and E terms) without the collocated potential: the
+// kinetic part of an operator whose potential term is given elsewhere
+cudaError_t hx_op_nopot(Ctx *c, const HxArgs<double> &a, cudaStream_t s) {
+  if (uses_sweep(c, a)) {
+    const std::pair<int, int> cfg = sweep_config(c, (const double *)nullptr, a, s);
+    return launch_hx_sweep(c->g, (const double *)nullptr, a, c->status + kStWaitHxSweep,
+                           cfg.first, cfg.second, s);
+  }
+  return launch_hx(c->g, nullptr, a, s);
+}
+cudaError_t hx_op_nopot(Ctx *c, const HxArgs<float> &a, cudaStream_t s) {
+  if (uses_sweep(c, a)) {
+    const std::pair<int, int> cfg = sweep_config(c, (const float *)nullptr, a, s);
+    return launch_hx_sweep(c->g, (const float *)nullptr, a, c->status + kStWaitHxSweep,
+                           cfg.first, cfg.second, s);
+  }
+  return launch_hx(c->g, nullptr, a, s);
+}
 cudaError_t hx_op(Ctx *c, const HxArgs<float> &a, cudaStream_t s) { return hx_op_t(c, a, s); }
 
 }  // namespace invdft

@@ -157,7 +157,7 @@ struct SweepArgs {
   const T *W;
   const float *E;
   const double *escale;
-  const T *v;                 // potential (FP32 copy on the FP32 path)
+  const T *v;                 // potential (FP32 copy on the FP32 path); null: none
   const double *shift_col;
   double shift, alpha, beta;
   int *err;                   // set to 3 when a wait for a TMA plane gives up
@@ -483,7 +483,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
 #pragma unroll
       for (int yi = 0; yi < P; ++yi) {
         const int uy = gy0 + jy * P + yi;
-        vv[yi] = (zin && ux < p.nx && uy < p.ny)
+        vv[yi] = (p.v && zin && ux < p.nx && uy < p.ny)
                      ? p.v[(size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)]
                      : (T)0;
       }

@@ -72,6 +72,10 @@ struct Tables {
   AxisTab ax[3];                      // x, y, z
 };
 void build_reference(int p, Tables *t);
+// ng-point Gauss-Legendre rule on [-1, 1] and the order-p GLL Lagrange basis at
+// its points: phi[k * (p+1) + j] = l_j(x_k)
+void gauss_lagrange(int p, int ng, std::vector<double> *xg, std::vector<double> *wg,
+                    std::vector<double> *phi);
 void build_axis(const Tables &ref, const std::vector<double> &breaks, int p, AxisTab *ax);
 
 // Bump allocator over the caller's workspace.
@@ -247,6 +251,9 @@ cudaError_t launch_hx(const Geom &g, const double *v, const HxArgs<float> &a, cu
 // launch_hx on the handle's operator, timed with CUDA events when profiling is on
 cudaError_t hx_op(Ctx *c, const HxArgs<double> &a, cudaStream_t s);
 cudaError_t hx_op(Ctx *c, const HxArgs<float> &a, cudaStream_t s);
+// the same without the collocated potential term (dense cell potentials)
+cudaError_t hx_op_nopot(Ctx *c, const HxArgs<double> &a, cudaStream_t s);
+cudaError_t hx_op_nopot(Ctx *c, const HxArgs<float> &a, cudaStream_t s);
 cudaError_t prof_flush(Ctx *c);
 // tensor-core (tcgen05, TF32) H~X for Q4 cells (hx_tc.cu)
 void build_tc_cell_matrix(const Geom &g, std::vector<float> *out);

@@ -126,6 +126,25 @@ void build_reference(int p, Tables *t) {
     }
 }
 
+void gauss_lagrange(int p, int ng, std::vector<double> *xg, std::vector<double> *wg,
+                    std::vector<double> *phi) {
+  const int q = p + 1;
+  std::vector<double> xn, wn;
+  gll(p, &xn, &wn);
+  gauss(ng, xg, wg);
+  std::vector<double> lam(q, 1.0);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j)
+      if (j != i) lam[i] /= (xn[i] - xn[j]);
+  phi->assign((size_t)ng * q, 0.0);
+  for (int k = 0; k < ng; ++k) {
+    // Gauss points are never GLL nodes (interior of [-1, 1], distinct roots)
+    double den = 0.0;
+    for (int j = 0; j < q; ++j) den += lam[j] / ((*xg)[k] - xn[j]);
+    for (int j = 0; j < q; ++j) (*phi)[(size_t)k * q + j] = (lam[j] / ((*xg)[k] - xn[j])) / den;
+  }
+}
+
 void build_axis(const Tables &ref, const std::vector<double> &breaks, int p, AxisTab *ax) {
   const int q = p + 1;
   const int ncell = (int)breaks.size() - 1;
