@@ -20,6 +20,7 @@ constexpr int kMaxGram = 128;       // widest block of Gram / rotation work
 constexpr int kMaxDense = 96;       // widest subspace of the one-CTA dense eigensolver
 constexpr int kMaxGroup = 16;       // largest degenerate set handled by the projections
 constexpr int kGramBlocks = 296;    // 2 x 148 SMs: partial sums of tall-skinny reductions
+constexpr int kMaxFilterDeg = 128;  // highest Chebyshev degree a forward-solve pass raises to
 
 // Device status words of the kernels with bounded waits (non-zero: a wait gave
 // up; the solvers read them back with their convergence data)
