@@ -183,7 +183,17 @@ def build_problem(wl, prec, device):
                     w=torch.ones(pb.L, dtype=torch.float64, device=device))
 
 
-def hx_benchmark(device, reps32=20, reps64=3):
+def measured_rates():
+    """Arithmetic rates of this device (TFLOP/s) from the library's probes:
+    FP64 FMA, FP32 FMA, packed FP32 FMA pairs, TF32 tensor-core MMAs."""
+    import paper_2510_10529_b300 as P
+    try:
+        return {k: P.invdft_peak_probe(k) for k in ("fp64", "fp32", "fp32x2", "tf32")}
+    except Exception as exc:      # a probe failure must not lose the bench line
+        return {"error": repr(exc)}
+
+
+def hx_benchmark(device, reps32=20, reps64=3, rates=None):
     """H~X on the 32^3-cell Q4 operator benchmark (64 unit-norm random vectors):
     TF32 tensor cores (dense cell GEMM), FP32 and FP64 sweep form (CUDA cores).
     Each timing is the mean over `reps` back-to-back launches after warm-up;
@@ -221,6 +231,14 @@ def hx_benchmark(device, reps32=20, reps64=3):
         byt = (2 * 64 * X.element_size() + vbytes) * pb.L
         out[name] = {"ms": ms, "tflops_nominal": flops / ms / 1e9, "gbs": byt / ms / 1e6,
                      "hbm_frac": byt / ms / 1e6 / hbm, "algorithmic_bytes": byt}
+        if name == "fp64" and rates and "fp64" in rates:
+            # the FP64 sweep executes about 100 FLOP per (node, column) (the
+            # seven even/odd banded sweeps, the partial cells at tile edges and
+            # the x halo): its rate against the measured FP64 FMA rate
+            ex = 100.0 * pb.L * 64
+            out[name]["fp64_pipe"] = {"executed_flops_est": ex, "tflops": ex / ms / 1e9,
+                                      "peak_tflops": rates["fp64"],
+                                      "frac": ex / ms / 1e9 / rates["fp64"]}
         if name != "tf32":
             out[name]["tuned_variant_seglen"] = pb.hx_config(64, name == "fp64")["plain"]
     pb.close()
@@ -540,7 +558,8 @@ def run_ours(args, rank, world):
                 "peak_source": "measured" if pk else "fallback",
                 "algorithmic_bytes_per_launch": km["algorithmic_bytes_per_launch"]}
     col_applies = sum(prof[k]["flops"] for k in prof) / (2.0 * ne * ne * cells)
-    hx = None if args.no_hx else hx_benchmark(device)
+    rates = measured_rates()
+    hx = None if args.no_hx else hx_benchmark(device, rates=rates)
     fp64 = None
     if args.prec == "mixed" and args.fp64_steps > 0 and not args.ncell:
         pb.close()
@@ -564,6 +583,7 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk, "hx": hx, "fp64_gpu": fp64, "small_workload_gpu": small,
+        "measured_rates_tflops": rates,
         "hx_in_step": {"minres": km, "filter": kf, "filter_tf32": kt},
         "step_stats": {"loss_last": stats[-1]["loss"], "err_l2_last": stats[-1]["err_l2"],
                        "err_l2": traj,

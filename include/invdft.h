@@ -296,6 +296,16 @@ invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16);
 invdft_status invdft_tune_hx(invdft_handle h, int variant, int seglen, int *nvariants);
 invdft_status invdft_hx_config(invdft_handle h, int ncol, int fp64, int *variant_seglen);
 invdft_status invdft_kernel_launches(unsigned long long *count);
+/* invdft_peak_probe: the arithmetic rate of this device in TFLOP/s, measured
+ * at the clocks it runs at by a kernel that fills the GPU with independent
+ * operations on register (or shared-memory) operands and no memory traffic:
+ * kind 0 FP64 FMA, 1 FP32 FMA, 2 packed FP32 FMA pairs, 3 TF32 tensor-core
+ * MMAs of the H~X kernel's shape (M = 128, N = 64, K = 128).  These are the
+ * roofline denominators of kernels bound by arithmetic.  tflops (host) is
+ * written; ms_out (optional, host) receives the timed launch's duration.
+ * Synchronous; allocates a few bytes of scratch.  EINVAL for a bad kind,
+ * ECUDA on a CUDA error, ETIMEOUT if the tensor-core probe's wait gave up. */
+invdft_status invdft_peak_probe(int kind, double *tflops, double *ms_out, void *stream);
 invdft_status invdft_graph_stats(long long *out3);
 
 /* Allocation-free loss reduction.  The paper has no counterpart: this entry

@@ -177,6 +177,15 @@ def invdft_graph_stats() -> dict:
     return {"captured": int(out[0]), "replays": int(out[1]), "refused": int(out[2])}
 
 
+def invdft_peak_probe(kind: str) -> float:
+    """Measured arithmetic rate (TFLOP/s): "fp64", "fp32", "fp32x2" or "tf32"."""
+    k = {"fp64": 0, "fp32": 1, "fp32x2": 2, "tf32": 3}[kind]
+    t, ms = C.c_double(), C.c_double()
+    _ok("invdft_peak_probe", lib.invdft_peak_probe(k, C.byref(t), C.byref(ms), _stream()), None,
+        False)
+    return t.value
+
+
 def invdft_kernel_launches() -> int:
     n = C.c_ulonglong()
     lib.invdft_kernel_launches(C.byref(n))

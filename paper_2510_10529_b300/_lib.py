@@ -110,6 +110,7 @@ def _load():
         "invdft_tune_hx": [H, C.c_int, C.c_int, P],
         "invdft_hx_config": [H, C.c_int, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],
+        "invdft_peak_probe": [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P],
         "invdft_graph_stats": [P],
         "invdft_loss_reduce_noalloc": [P, P, P, P, C.c_longlong, P, P, P],
         "invdft_batch_create": [P, C.c_int, C.POINTER(H)],

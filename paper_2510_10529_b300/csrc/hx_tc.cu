@@ -459,4 +459,82 @@ cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a,
   return cudaGetLastError();
 }
 
+
+namespace {
+
+// Tensor-pipe rate probe: chains of the H~X kernel's MMA shape (M = 128,
+// N = 64, K = 128 as 16 steps of K = 8, kind::tf32) issued back to back by one
+// thread per CTA on operands resident in shared memory; no memory traffic.
+__global__ void __launch_bounds__(128, 1) tf32_probe_kernel(int chains, int *err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + kSmemA;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&tmem_slot)), "r"(kTcN) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int i = tid; i < (int)((kSmemA + kSmemB) / 16); i += 128)
+    reinterpret_cast<float4 *>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sB);
+    for (int c = 0; c < chains; ++c) {
+#pragma unroll
+      for (int j = 0; j < kTcK / 8; ++j) {
+        const uint64_t ad = make_desc(a_base + j * 256);
+        const uint64_t bd = make_desc(b_base + j * 256);
+        const uint32_t acc = (c | j) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred pa;\n setp.ne.b32 pa, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, pa;\n}\n"
+            :: "r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(&mbar)) : "memory");
+    uint32_t done = 0;
+    long long spins = 0;
+    while (!done) {
+      asm volatile(
+          "{\n .reg .pred pw;\n mbarrier.try_wait.parity.shared::cta.b64 pw, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, pw;\n}\n"
+          : "=r"(done) : "r"(smem_u32(&mbar)), "r"(0u) : "memory");
+      if (!done && ++spins > kSpinLimit) {
+        atomicExch(err, 1);
+        break;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTcN)
+                 : "memory");
+}
+
+}  // namespace
+
+// flops of one probe launch: grid CTAs x chains x 2 M N K
+cudaError_t launch_tf32_probe(int grid, int chains, int *err, double *flops, cudaStream_t s) {
+  const size_t smem = kSmemA + kSmemB;
+  cudaError_t e = raise_smem_limit(tf32_probe_kernel, smem);
+  if (e != cudaSuccess) return e;
+  ::invdft::count_launch();
+  tf32_probe_kernel<<<grid, 128, smem, s>>>(chains, err);
+  *flops = (double)grid * chains * 2.0 * kTcM * kTcN * kTcK;
+  return cudaGetLastError();
+}
+
 }  // namespace invdft

@@ -192,6 +192,8 @@ namespace invdft {
 
 // ------------------------------------------------------------ error helpers
 bool cuda_ok(Ctx *c, cudaError_t e, const char *what);
+// text of invdft_last_error(NULL) (failures with no handle)
+void set_global_error(const char *msg);
 // process-wide count of kernels this library has launched (benchmark evidence)
 void count_launch();
 // n kernels run by a graph replay (negative: take back launches counted while
@@ -262,6 +264,9 @@ size_t tc_cell_matrix_floats();
 cudaError_t launch_hx_tc(const Geom &g, const double *v, const HxArgs<float> &a, const float *Ke,
                          const int *perm, int *err, cudaStream_t s);
 void build_cell_order(int nc, std::vector<int> *perm);
+// tensor-pipe rate probe (M = 128, N = 64, K = 128 TF32 MMA chains); err: set if
+// the final wait gave up; flops: the launch's floating-point operations
+cudaError_t launch_tf32_probe(int grid, int chains, int *err, double *flops, cudaStream_t s);
 // Owner-computes sweep form of H~X (hx_sweep.cu): FP32 and FP64 blocks on
 // orders 2 and 4, ncol * elem a multiple of 16 bytes, 16-byte aligned blocks,
 // Z not aliasing X, W or E.  variant in [0, sweep_variants) selects the tile
