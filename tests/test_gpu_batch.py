@@ -131,3 +131,68 @@ def test_batch_phase_wait_timeout_is_reported(cases):
     assert all(s == 0 for s in status), status
     assert all(np.isfinite(st["loss"]) for st in stats)
     batch.close()
+
+
+def _batch16_shaped():
+    """The sixteen problems of the batched workload (workloads.batch16: its
+    seeded orders, electron counts, nuclei, bumps, widths, degree and kT) on
+    meshes of 3 to 5 cells per axis, which the oracle steps in seconds."""
+    out = []
+    for wl in W.batch16():
+        n = 3 + wl.ncell % 3
+        mesh = fe.Mesh(wl.lo, wl.hi, n, wl.order)
+        xyz = mesh.coords()
+        v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
+        bump = W.gaussian_bumps(xyz, wl.bump_c, wl.bump_a, wl.bump_b)
+        rho_d = ks.forward(mesh, v + bump, wl.n_electrons, wl.nstates, wl.kT)["rho"]
+        op = inverse.Problem(mesh=mesh, v_fixed=v, rho_data=rho_d, w=np.ones(mesh.L),
+                             n_electrons=wl.n_electrons, nstates=wl.nstates, kT=wl.kT)
+        loss0 = inverse.evaluate(op, np.zeros(mesh.L), with_grad=False)[0]
+        out.append((wl, n, mesh, v, rho_d, op, loss0))
+    return out
+
+
+def test_sixteen_problem_batch_follows_the_oracle():
+    """All sixteen problems of the batched workload's recipe stepped twice as
+    one batch (persistent filter kernel); every problem's v_xc and loss follow
+    the oracle's L-BFGS trajectory (1e-6 relative)."""
+    import paper_2510_10529_b300 as P
+    cases16 = _batch16_shaped()
+    problems = []
+    for wl, n, mesh, v, _, _, _ in cases16:
+        pb = P.Problem(wl.lo, wl.hi, n, wl.order, wl.nstates, n_electrons=wl.n_electrons,
+                       kT=wl.kT, prec="mixed", cheb_degree=wl.cheb_degree, eig_tol=1e-10,
+                       adj_tol=1e-11)
+        pb.set_potential(_cuda(v))
+        problems.append(pb)
+    batch = P.Batch(problems)
+    v_xc = [_cuda(np.zeros(c[2].L)) for c in cases16]
+    rd = [_cuda(c[4]) for c in cases16]
+    w = [_cuda(np.ones(c[2].L)) for c in cases16]
+    states = [inverse.State(v_xc=np.zeros(c[2].L)) for c in cases16]
+    worst = 0.0
+    compared = set()
+    for _ in range(2):
+        stats, status = batch.step(rd, w, v_xc)
+        assert all(s == 0 for s in status), status
+        for b, c in enumerate(cases16):
+            states[b] = inverse.step(c[5], states[b])
+            if c[6] < 1e-6:
+                # the start already reproduces rho_data to ~1e-3 in L2 (the bump
+                # barely moves the density on this coarse mesh): the first
+                # step's direction and the line search's decisions then rest
+                # on losses that differ at rounding level, on both sides, so
+                # the trajectory is not reproducible; these problems are only
+                # required to step without error
+                assert np.isfinite(stats[b]["loss"]), b
+                continue
+            compared.add(b)
+            ref = states[b].v_xc
+            err = np.linalg.norm(v_xc[b].cpu().numpy() - ref) / np.linalg.norm(ref)
+            worst = max(worst, err)
+            assert err <= 1e-6, (b, err)
+            assert abs(stats[b]["loss"] - states[b].loss) <= 1e-6 * states[b].loss, b
+    assert len(compared) >= 10, compared
+    print(f"16-problem batch: {len(compared)} trajectories compared, worst v_xc rel err "
+          f"{worst:.2e}, info {batch.info()}")
+    batch.close()
