@@ -65,11 +65,10 @@ METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 # DRAM bytes per (node, column) of one FP32 sweep-form H~X launch of the MINRES
 # kind (plain epilogue, no W / E): ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of hx_sweep_kernel on the 24^3-cell Q4 mesh (857,375
-# unknowns) with 52 columns, in the tile variant and z-segment length the
-# autotuner picks for the in-step launches (profiles/hx_sweep_cube24_q4_52cols.md).
-# None until that capture exists for the current kernel.
-HX_SWEEP_DRAM_BYTES_PER_NODE_COL = None
-HX_SWEEP_DRAM_SOURCE = "profiles/hx_sweep_cube24_q4_52cols.md"
+# unknowns) with 60 columns, tile variant 2, z segments of 6 cells
+# (profiles/hx_sweep_cube24_q4_60cols.md): 244,695,808 + 169,892,608 bytes.
+HX_SWEEP_DRAM_BYTES_PER_NODE_COL = (244695808 + 169892608) / (857375 * 60)
+HX_SWEEP_DRAM_SOURCE = "profiles/hx_sweep_cube24_q4_60cols.md"
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -88,6 +87,10 @@ def parse():
     ap.add_argument("--ncell", type=int, default=None,
                     help="run the workload on NCELL^3 cells of the same box (a smaller case "
                          "for kernel profiles; the printed line then names that mesh)")
+    ap.add_argument("--hx-variant", type=int, default=-1,
+                    help="with --hx-case: fix the sweep kernel's tile variant (-1: autotuned)")
+    ap.add_argument("--hx-seglen", type=int, default=0,
+                    help="with --hx-case: fix the sweep kernel's z-segment length (0: autotuned)")
     ap.add_argument("--oracle-iterations", nargs=2, metavar=("BUDGET_S", "MAX"), default=None,
                     help=argparse.SUPPRESS)
     ap.add_argument("--hx-case", nargs=3, metavar=("NCELL", "NCOL", "KIND"), default=None,
@@ -246,7 +249,7 @@ def hx_benchmark(device, reps32=20, reps64=3, rates=None):
             "peak_gbs": hbm, "peak_source": "measured" if pk else "fallback", **out}
 
 
-def hx_case(ncell, ncol, kind, device):
+def hx_case(ncell, ncol, kind, device, variant=-1, seglen=0):
     """Three H~X applications on an ncell^3 Q4 mesh of the operator-benchmark box
     (a small case that a kernel profiler can capture in seconds)."""
     import torch
@@ -257,6 +260,7 @@ def hx_case(ncell, ncol, kind, device):
     xyz = pb.coords()
     v = W.smeared_coulomb(xyz, wl.nuclei_R, wl.nuclei_Z, wl.smear)
     pb.set_potential(torch.as_tensor(v, dtype=torch.float64, device=device))
+    pb.tune_hx(variant, seglen)
     X = torch.as_tensor(W.random_block(pb.L, ncol, wl.seed), device=device)
     if kind != "fp64":
         X = X.float()
@@ -265,7 +269,8 @@ def hx_case(ncell, ncol, kind, device):
         P.invdft_apply_h(pb.h, X, Y, kind == "tf32")
     torch.cuda.synchronize()
     pb.close()
-    print(json.dumps({"hx_case": {"ncell": ncell, "unknowns": pb.L, "ncol": ncol, "kind": kind}}))
+    print(json.dumps({"hx_case": {"ncell": ncell, "unknowns": pb.L, "ncol": ncol, "kind": kind,
+                                  "variant": variant, "seglen": seglen}}))
 
 
 # ------------------------------------------------------------------ oracle baseline
@@ -485,6 +490,11 @@ def run_ours(args, rank, world):
     # device time of the step alone (value) and wall time with the copies (e2e)
     v_host = v_xc.cpu().pin_memory()
     torch.cuda.synchronize()
+    # INVDFT_PROFILE_TIMED=1 brackets the timed steps for a profiler started
+    # with capture off (ncu --profile-from-start off); it changes no work
+    profile_timed = os.environ.get("INVDFT_PROFILE_TIMED") == "1"
+    if profile_timed:
+        torch.cuda.profiler.start()
     dev_ms, wall_s, stats = 0.0, 0.0, []
     for _ in range(args.steps):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -500,6 +510,8 @@ def run_ours(args, rank, world):
         dev_ms += e0.elapsed_time(e1)
         stats.append(st)
         traj.append(st["err_l2"])
+    if profile_timed:
+        torch.cuda.profiler.stop()
     launches = P.invdft_kernel_launches() - launches0
     prof = pb.profile_hx(False)
     clk = clocks.stop()
@@ -737,7 +749,7 @@ def main():
         n, k, kind = args.hx_case
         if kind not in ("tf32", "fp32", "fp64"):
             raise SystemExit("--hx-case KIND must be tf32, fp32 or fp64")
-        hx_case(int(n), int(k), kind, "cuda")
+        hx_case(int(n), int(k), kind, "cuda", args.hx_variant, args.hx_seglen)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
