@@ -378,8 +378,10 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
         const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
         V val = a[yi];
         if constexpr (GR) val = vmul((T)(dxy[yi] * p.dn[2][g]), val);
-        if (HW) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
-        if constexpr (HE) val = vfmav(esc, eload<V>(p.E + off), val);
+        // graded meshes add beta W + E here; uniform ones fold them into the
+        // nodal term of their plane
+        if constexpr (HW && GR) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
+        if constexpr (HE && GR) val = vfmav(esc, eload<V>(p.E + off), val);
         *reinterpret_cast<V *>(p.Z + off) = val;
       }
     }
@@ -488,6 +490,25 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
                      : (T)0;
       }
     }
+    // uniform meshes: W and E of this plane at the thread's owned nodes, loaded
+    // here and consumed with the nodal term after the y sweep
+    constexpr bool kFold = (HW || HE) && !GR;
+    V wr[kFold ? P : 1], er[kFold ? P : 1];
+    if constexpr (kFold) {
+      const int uz = gz - 1;
+      const bool own = gz > n0 * P && gz <= gz_end && uz < p.nz;
+#pragma unroll
+      for (int yi = 0; yi < P; ++yi) {
+        const int uy = gy0 + jy * P + yi;
+        wr[yi] = vzero<V>();
+        er[yi] = vzero<V>();
+        if (own && cx_in && uy < p.ny) {
+          const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
+          if constexpr (HW) wr[yi] = *reinterpret_cast<const V *>(p.W + off);
+          if constexpr (HE) er[yi] = eload<V>(p.E + off);
+        }
+      }
+    }
 
     // ---- y sweep: R = B^y Px + A^y Qx, S = B^y Qx at this thread's p nodes
     V R[P], Sv[P];
@@ -546,6 +567,8 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       nod[yi] = vfmav(vrsub(alpha * vv[yi], ash), xv, vzero<V>());
       // graded meshes: carried divided by D (restored at the output)
       if constexpr (GR) nod[yi] = vmul((T)(sxy[yi] * p.m1[2][gz] * p.dn[2][gz]), nod[yi]);
+      if constexpr (kFold && HW) nod[yi] = vfma(beta, wr[yi], nod[yi]);
+      if constexpr (kFold && HE) nod[yi] = vfmav(esc, er[yi], nod[yi]);
     }
 
     // ---- z: accumulate the planes of the current z-cell

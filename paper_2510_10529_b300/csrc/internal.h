@@ -27,7 +27,8 @@ constexpr int kMaxFilterDeg = 128;  // highest Chebyshev degree a forward-solve 
 constexpr int kStWaitHxTc = 8;      // H~X on the tensor cores
 constexpr int kStWaitHxSweep = 9;    // H~X in the sweep form (TMA plane loads)
 constexpr int kStWaitGram = 10;     // deflation Gram on the tensor cores
-constexpr int kStWaitCount = 3;
+constexpr int kStWaitUpdate = 11;   // deflation update on the tensor cores
+constexpr int kStWaitCount = 4;
 
 // Geometry and 1D factors of the cell operator, passed to kernels by value.
 // A cell is a box with sizes (h_x, h_y, h_z); with A, B the 1D GLL stiffness
@@ -319,6 +320,14 @@ cudaError_t launch_defl_update_f32(const float *Psi, int n1p, const double *C, i
 // an MMA wait gave up.
 cudaError_t launch_defl_gram_tc(const float *Psi, int n1p, const float *Z, int n2p, long long L,
                                 double *G, double *partial, int *err, int nsm, cudaStream_t s);
+// Tensor-core version of launch_defl_update_f32 (deflate_tc.cu): Z += alpha
+// Psi C with C^T and Psi split in two TF32 terms (three products), Psi read by
+// one TMA tensor copy per 128-node tile; partial holds nsm * n2p doubles; err:
+// device word set to 5 if a wait gave up.
+cudaError_t launch_defl_update_tc(const float *Psi, int n1p, const double *C, int n2p,
+                                  long long L, float *Z, double alpha, const float *V,
+                                  double *dot_out, double *partial, int *err, int nsm,
+                                  cudaStream_t s);
 // out[e] = sum_b partial[b * n + e], b < nblk
 cudaError_t launch_sum_partials(const double *partial, int nblk, int n, double *out,
                                 cudaStream_t s);

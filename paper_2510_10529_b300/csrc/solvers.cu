@@ -73,7 +73,7 @@ invdft_status fetch_many(Ctx *c, std::initializer_list<Piece> pieces, cudaStream
 // read the words back with their convergence data.
 invdft_status check_waits(Ctx *c, const int *w) {
   static const char *const what[kStWaitCount] = {"H~X (tensor cores)", "H~X (sweep form)",
-                                                 "deflation Gram"};
+                                                 "deflation Gram", "deflation update"};
   for (int i = 0; i < kStWaitCount; ++i)
     if (w[i]) {
       c->err = std::string("a bounded device wait gave up in ") + what[i];
@@ -127,8 +127,13 @@ double tridiag_max_eig(const std::vector<double> &d, const std::vector<double> &
 }
 
 // Upper bound of the spectrum of H~: k-step Lanczos, max Ritz value + |f|.
+// With two or more states the chain runs on a two-column block, i.e. on
+// H~ (+) H~, whose spectrum is that of H~: the block's H~X takes the
+// owner-computes sweep form (deterministic, no scatter), which one FP64
+// column cannot (its rows are narrower than a bulk copy's 16-byte unit).
 invdft_status upper_bound(Ctx *c, cudaStream_t s, double *out) {
-  const long long L = c->L;
+  const int nc = c->nv >= 2 ? 2 : 1;
+  const long long L = c->L * nc;
   double *v0 = (double *)c->C0, *v = (double *)c->C1, *f = (double *)c->C2, *sc = c->scal + kScMisc;
   CU(launch_fill_random(v, L, c->o.seed ^ 0xA5A5A5A5ULL, s), "fill_random");
   CU(launch_dot(v, v, L, sc, c->partial, s), "dot");
@@ -143,7 +148,7 @@ invdft_status upper_bound(Ctx *c, cudaStream_t s, double *out) {
     HxArgs<double> a;
     a.X = v;
     a.Z = f;
-    a.ncol = 1;
+    a.ncol = nc;
     a.W = v0;
     a.beta = -beta;                  // f = H v - beta v0
     CU(hx_op(c, a, s), "hx(lanczos)");
@@ -479,12 +484,13 @@ invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s
   }
   // padded FP32 blocks (Psi width a multiple of 8, Z width of 4)
   if (no >= 16) {
-    // Gram on the tensor cores (tcgen05, both operands split into two TF32
-    // terms); update with the fused dot on the CUDA cores
+    // Gram and update on the tensor cores (tcgen05, operands split into two
+    // TF32 terms), the column dot fused into the update
     CU(launch_defl_gram_tc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial,
                            c->status + kStWaitGram, c->nsm, s), "gram(deflate)");
-    CU(launch_defl_update_f32((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
-                              (const float *)V, dot, c->partial, s), "update(deflate)");
+    CU(launch_defl_update_tc((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
+                             (const float *)V, dot, c->partial, c->status + kStWaitUpdate,
+                             c->nsm, s), "update(deflate)");
   } else {
     // narrow blocks: one row per thread keeps every thread busy
     CU(launch_defl_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),
