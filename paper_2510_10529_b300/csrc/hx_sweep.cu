@@ -306,6 +306,10 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
   __shared__ __align__(8) uint64_t full[NST];
   __shared__ T sash[C], sesc[C];
   __shared__ int abort_flag;
+  // potential at the owned nodes of a plane, one plane ahead: element copies
+  // (cp.async) into a two-plane ring, completed before the barrier that
+  // precedes their use; zero where there is no potential or no unknown
+  __shared__ __align__(16) T vring[2][TX * TY];
   const SweepCoef<CT, P> &cf = p.cf;
   const int tid = threadIdx.x;
 
@@ -331,6 +335,23 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
     sash[j] = (T)(p.alpha * sh);
     sesc[j] = (HE && in) ? (T)(p.alpha * p.escale[col]) : (T)0;
   }
+  auto fetch_v = [&](int gzp, int buf) {
+    const int uz = gzp - 1;
+    for (int e = tid; e < TX * TY; e += NTH) {
+      const int lx = e % TX, ly = e / TX;
+      const int vx = gx0 + lx, vy = gy0 + ly;
+      T *dst = &vring[buf][e];
+      if (p.v && uz >= 0 && uz < p.nz && vx < p.nx && vy < p.ny)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                     :: "r"(smem_u32(dst)),
+                        "l"(p.v + (size_t)vx + (size_t)p.nx * ((size_t)vy + (size_t)p.ny * uz)),
+                        "n"((int)sizeof(T)) : "memory");
+      else
+        *dst = (T)0;
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  fetch_v(gz_begin, 0);
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < NST; ++s)
@@ -340,6 +361,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       load_plane(&tmx, stage0 + s * S::STAGE_STRIDE_V, &full[s], kStageBytes, c0, gx0 - 1,
                  gy0 - 1, gz_begin + s - 1);
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
 
   // this thread's y/z task: owned x, a y-cell, a column pair
@@ -477,19 +499,12 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
     const V *stg = stage0 + s * S::STAGE_STRIDE_V;
     const V *Pr = Px + (it & 1) * 2 * RY * PXS;
     const V *Qr = Pr + RY * PXS;
-    // potential of this plane at the thread's nodes, loaded ahead of its use
+    // potential of the next plane into the other ring slot (its readers
+    // passed the last barrier); this plane's from the ring
+    if (it + 1 < nplanes) fetch_v(gz + 1, (it + 1) & 1);
     T vv[P];
-    {
-      const int uz = gz - 1;
-      const bool zin = uz >= 0 && uz < p.nz;
 #pragma unroll
-      for (int yi = 0; yi < P; ++yi) {
-        const int uy = gy0 + jy * P + yi;
-        vv[yi] = (p.v && zin && ux < p.nx && uy < p.ny)
-                     ? p.v[(size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)]
-                     : (T)0;
-      }
-    }
+    for (int yi = 0; yi < P; ++yi) vv[yi] = vring[it & 1][(jy * P + yi) * TX + ox];
     // uniform meshes: W and E of this plane at the thread's owned nodes, loaded
     // here and consumed with the nodal term after the y sweep
     constexpr bool kFold = (HW || HE) && !GR;
@@ -647,6 +662,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
       V *Pw = Px + ((it + 1) & 1) * 2 * RY * PXS;
       xsweep(stage0 + s1 * S::STAGE_STRIDE_V, Pw, Pw + RY * PXS, gz + 1);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     // the stage of plane it is free: fetch the plane NST ahead into it
     if (tid == 0 && it + NST < nplanes) {
@@ -655,6 +671,7 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
                  gy0 - 1, gz + NST - 1);
     }
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (abort_flag && tid == 0) {
     // a plane never arrived: report, and give the loads still in flight a
     // bounded chance to land before the CTA's shared memory is released
