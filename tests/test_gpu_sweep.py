@@ -79,3 +79,35 @@ def test_sweep_filter_epilogue_matches_oracle(seglen, dtype, tol):
     err = _colrel(Yg, Y_ora)
     print(f"sweep filter seglen={seglen} {dtype}: {err:.2e}")
     assert err <= tol
+
+
+@pytest.mark.parametrize("ncell,order", [(4, 4), (3, 6)])
+def test_every_variant_in_the_defect_corrected_filter(ncell, order):
+    """Each FP32 tile variant carries the defect-corrected Chebyshev filter
+    (beta W and E terms) of a mixed forward solve: eigenvalues of the occupied
+    states within 1e-6 Ha and the density within 1e-6 (L2) of the oracle's."""
+    import math
+
+    import paper_2510_10529_b300 as P
+    from oracle import ks
+    lo, hi = -6.0, 6.0
+    mesh = fe.Mesh(lo, hi, ncell, order)
+    xyz = mesh.coords()
+    v = W.smeared_coulomb(xyz, np.array([[0.2, -0.3, 0.1]]), np.array([4.0]), 0.5)
+    Ne, nst = 4.0, 8
+    ref = ks.forward(mesh, v, Ne, nst, 0.0)
+    m = mesh.mass()
+    pb = P.Problem(lo, hi, ncell, order, nstates=nst, n_electrons=Ne, kT=0.0, prec="mixed",
+                   eig_tol=1e-10, adj_tol=1e-11, cheb_degree=20)
+    pb.set_potential(_cuda(v))
+    n32, _ = pb.tune_hx(-1, 0)
+    for variant in range(n32):
+        pb.tune_hx(variant, 0)
+        pb.reset()                      # cold start: every variant runs the full filter
+        out = pb.forward_solve()
+        assert out["stats"]["cheb_passes"] >= 2
+        deps = float(np.max(np.abs(out["eps"].cpu().numpy()[:2] - ref["eps"][:2])))
+        drho = math.sqrt(np.sum(m * (out["rho"].cpu().numpy() - ref["rho"]) ** 2))
+        print(f"defect filter p={order} variant={variant}: deps={deps:.2e} drho={drho:.2e}")
+        assert deps <= 1e-6
+        assert drho <= 1e-6
