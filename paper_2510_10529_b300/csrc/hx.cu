@@ -327,8 +327,10 @@ std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStr
   if (it != c->hx_tuned.end()) {
     return {fv >= 0 ? fv : it->second.first, fs > 0 ? fs : it->second.second};
   }
-  const std::pair<int, int> dflt{fv >= 0 ? fv : 0, fs > 0 ? fs : nc};
-  if (c->L < (1LL << 18)) return dflt;
+  // default: segments short enough for two CTAs per SM (a negative length is
+  // resolved per launch from the variant's tile count)
+  const int par = -2 * std::max(c->nsm, 1);
+  const std::pair<int, int> dflt{fv >= 0 ? fv : 0, fs > 0 ? fs : par};
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return dflt;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -338,10 +340,10 @@ std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStr
   }
   std::pair<int, int> best = dflt;
   float best_ms = 1e30f;
-  const int segs[3] = {nc, (nc + 1) / 2, (nc + 3) / 4};
+  const int segs[4] = {nc, (nc + 1) / 2, (nc + 3) / 4, par};
   for (int var = 0; var < nvar; ++var) {
     if (fv >= 0 && var != fv) continue;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       const int seg = fs > 0 ? fs : segs[k];
       if (fs > 0 && k > 0) break;
       if (k > 0 && segs[k] == segs[k - 1]) continue;

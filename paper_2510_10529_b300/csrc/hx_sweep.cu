@@ -806,6 +806,12 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   sa.ntx = (g.n[0] + TX - 1) / TX;
   sa.nty = (g.n[1] + TY - 1) / TY;
   sa.nchunk = (a.ncol + C - 1) / C;
+  if (seglen < 0) {
+    // the segment length that gives at least -seglen work items (CTAs)
+    const long long per = (long long)sa.ntx * sa.nty * sa.nchunk;
+    const long long nseg = std::min<long long>(g.nc[2], std::max<long long>(1, (-(long long)seglen + per - 1) / per));
+    seglen = (int)((g.nc[2] + nseg - 1) / nseg);
+  }
   sa.seglen = std::max(1, std::min(seglen, g.nc[2]));
   const int nseg = (g.nc[2] + sa.seglen - 1) / sa.seglen;
   const long long nitems = (long long)sa.ntx * sa.nty * sa.nchunk * nseg;
