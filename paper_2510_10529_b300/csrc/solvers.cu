@@ -409,12 +409,15 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
     // damps the top of a very wide wanted interval below FP64 resolution) is
     // repeated from the same Ritz vectors with half the degree; Rayleigh-Ritz
     // fails before it overwrites them
-    // the first two passes of a solve use the configured degree m, later ones
-    // 2m: near the cut the filter's gain grows with the square of the degree,
-    // so one pass of 2m does the work of about four of m at twice the filter
-    // cost and one Rayleigh-Ritz instead of four (the states that still need
-    // passes after two are those close to the top of the block)
-    const int m0 = pass >= 2 ? std::min(2 * c->o.cheb_degree, kMaxFilterDeg) : c->o.cheb_degree;
+    // the first two passes of a solve use the configured degree m, the third
+    // 2m and later ones 4m (at most kMaxFilterDeg): near the cut the filter's
+    // gain grows with the square of the degree, so one pass of 2m does the
+    // work of about four of m at twice the filter cost and one Rayleigh-Ritz
+    // instead of four (the states that still need passes after two are those
+    // close to the top of the block; Rayleigh-Ritz in FP64 costs about as much
+    // as a degree-60 FP32 filter here)
+    const int m1 = c->o.cheb_degree;
+    const int m0 = pass < 2 ? m1 : std::max(m1, std::min((pass == 2 ? 2 : 4) * m1, kMaxFilterDeg));
     for (int m = m0;; m = std::max(1, m / 2)) {
       if (c->o.prec == INVDFT_FP64) {
         TRY(run_filter(c, c->X, c->Y, n, m, a, b, a0, INVDFT_FP64, nullptr, nullptr, s));
