@@ -138,6 +138,7 @@ size_t plan(Ctx *c, char *base) {
   c->grad_new = ar.take<double>(L);
   c->dir = ar.take<double>(L);
   c->vtry = ar.take<double>(L);
+  c->v_ub = ar.take<double>(L);
   c->dLdrho = ar.take<double>(L);
   c->X = ar.take<double>(blk);
   c->Y = ar.take<double>(blk);
@@ -373,6 +374,7 @@ invdft_status invdft_bind_workspace(invdft_handle h, void *device_ptr, size_t by
   h->have_forward = false;
   h->have_grad = false;
   h->have_upper = false;
+  h->have_ub_base = false;
   h->hist_n = h->hist_head = 0;
   return INVDFT_OK;
 }
@@ -472,6 +474,7 @@ invdft_status invdft_reset(invdft_handle h) {
   h->have_forward = false;
   h->have_grad = false;
   h->have_upper = false;
+  h->have_ub_base = false;
   h->hist_n = h->hist_head = 0;
   return INVDFT_OK;
 }

@@ -136,6 +136,12 @@ struct Ctx {
   size_t ws_bytes = 0;
   Arena ar;
   double upper_bound = 0.0;         // cached spectral upper bound of H~
+  // the last Lanczos bound and the potential it was taken at: a later
+  // potential v bounds the spectrum by ub_base + max |v - v_ub| (Weyl)
+  double ub_base = 0.0;
+  bool have_ub_base = false;
+  int ub_reuse = 0;
+  double *v_ub = nullptr;
   double eig_tol_used = 0.0;        // eigen tolerance of the last forward solve
   bool have_upper = false;
 

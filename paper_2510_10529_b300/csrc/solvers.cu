@@ -369,8 +369,31 @@ invdft_status forward_solve(Ctx *c, invdft_stats *stats, cudaStream_t s) {
     TRY(rayleigh_ritz(c, s));
   }
   if (!c->have_upper) {
-    TRY(upper_bound(c, s, &c->upper_bound));
-    hx_calls += 12;
+    // Weyl: the potential enters H~ as diag(v), so a change of v moves the
+    // top of the spectrum by at most max |dv|.  Up to kUbReuse solves reuse
+    // the last Lanczos bound plus that shift; then the bound is taken again.
+    constexpr int kUbReuse = 8;
+    bool reused = false;
+    if (c->have_ub_base && c->ub_reuse < kUbReuse) {
+      double *dv = (double *)c->C2;     // free before the filter runs
+      CU(launch_lincomb(1.0, c->v, -1.0, c->v_ub, dv, L, s), "dv");
+      CU(launch_absmax(dv, L, c->scal + kScMisc, c->partial, s), "absmax(dv)");
+      double shift = 0.0;
+      TRY(fetch(c, c->scal + kScMisc, sizeof(double), &shift, s));
+      if (std::isfinite(shift)) {
+        c->upper_bound = c->ub_base + shift;
+        ++c->ub_reuse;
+        reused = true;
+      }
+    }
+    if (!reused) {
+      TRY(upper_bound(c, s, &c->upper_bound));
+      hx_calls += 12;
+      CU(cudaMemcpyAsync(c->v_ub, c->v, L * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+      c->ub_base = c->upper_bound;
+      c->have_ub_base = true;
+      c->ub_reuse = 0;
+    }
     c->have_upper = true;
   }
   const double tol = eig_tolerance(c);
