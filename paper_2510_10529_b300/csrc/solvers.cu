@@ -862,8 +862,11 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
       CU((launch_add_convert<double, double>(x64, Po, (long long)blk, s)), "add");
     }
     total_iters += its;
-    TRY(deflate<double>(c, PsiD, nd, Po, no, s));
-    // r = Q b - Q (H~ - eps) Q p
+    // r = Q b - Q (H~ - eps) p: the inner solutions lie in range(Q) up to the
+    // inner precision, and the part of p along Psi that this leaves changes
+    // Q (H~ - eps) p only by Q (H~ Psi - Psi Lambda) c (the Ritz residuals
+    // times that part), far below the refinement tolerance; p itself is
+    // projected once after the loop
     HxArgs<double> a;
     a.X = Po;
     a.Z = r64;
@@ -875,6 +878,7 @@ invdft_status adjoint_solve(Ctx *c, const double *dLdrho, double *p_full, invdft
     CU(hx_op(c, a, s), "hx(residual)");
     TRY(deflate<double>(c, PsiD, nd, r64, no, s));
   }
+  TRY(deflate<double>(c, PsiD, nd, Po, no, s));
   // p~ = p_Q + Psi C  (Eq. 8 inside the degenerate set, exact ratios outside)
   CU(launch_rotate_acc<double>(PsiD, nd, dC, no, L, Po, 1.0, s), "along(psi)");
   if (p_full) {
