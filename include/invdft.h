@@ -285,16 +285,24 @@ invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16);
  * length (in cells) for every later H~X launch of this handle; -1 / 0 leave
  * them to the autotuner, which on the first launch of each (precision, ncol,
  * epilogue) that is not being captured into a graph times every variant with
- * the whole z range, halves, quarters, and segments short enough for two
- * CTAs per SM, and keeps the fastest (launches inside a capture before that
- * take variant 0 with the short segments).  nvariants (optional, host
- * int[2]) receives the number of FP32 and FP64 variants for this mesh order.
- * EINVAL for a NULL handle, seglen < 0 or a variant out of range.
+ * the whole z range, halves, quarters, segments short enough for two CTAs
+ * per SM and the balanced schedule, and keeps the fastest (launches inside a
+ * capture before that take variant 0 with the short segments).
+ * seglen = INVDFT_HX_SEG_BALANCED fixes the balanced schedule: a persistent
+ * grid of one CTA per resident slot that takes whole (tile, column chunk)
+ * units round-robin and then an equal share of the z-cells of the units left
+ * over, so that no second wave runs on part of the GPU (launches without the
+ * W and E terms on meshes of equal cells; others then run the whole z range
+ * per CTA).  nvariants (optional,
+ * host int[2]) receives the number of FP32 and FP64 variants for this mesh
+ * order.  EINVAL for a NULL handle, seglen < 0 or a variant out of range.
  * invdft_hx_config: the autotuned (variant, seglen) of this handle for a
  * width ncol and precision (fp64 != 0: FP64), for the four epilogues
  * {plain, E only, W only, W and E}: variant_seglen (host int[8]), -1 where
  * that configuration has not been tuned; a negative seglen -n means the
- * segment length is chosen per launch for at least n CTAs.                   */
+ * segment length is chosen per launch for at least n CTAs, and
+ * INVDFT_HX_SEG_BALANCED the balanced schedule.                              */
+#define INVDFT_HX_SEG_BALANCED 0x7fffffff
 invdft_status invdft_tune_hx(invdft_handle h, int variant, int seglen, int *nvariants);
 invdft_status invdft_hx_config(invdft_handle h, int ncol, int fp64, int *variant_seglen);
 invdft_status invdft_kernel_launches(unsigned long long *count);

@@ -14,11 +14,11 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_MIXED, INVDFT_MIXED_TF32, INVDFT_OK,
-                   InvdftError, MeshDesc, Opts, Stats, check, lib)
+from ._lib import (INVDFT_ENOCONV, INVDFT_FP64, INVDFT_HX_SEG_BALANCED, INVDFT_MIXED,
+                   INVDFT_MIXED_TF32, INVDFT_OK, InvdftError, MeshDesc, Opts, Stats, check, lib)
 
 __all__ = ["Problem", "Batch", "KohnShamDensity", "MeshDesc", "Opts", "Stats", "InvdftError",
-           "INVDFT_FP64", "INVDFT_MIXED", "INVDFT_MIXED_TF32", "library_path"]
+           "INVDFT_FP64", "INVDFT_HX_SEG_BALANCED", "INVDFT_MIXED", "INVDFT_MIXED_TF32", "library_path"]
 
 
 def library_path() -> str:

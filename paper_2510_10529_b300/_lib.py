@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libinvdft.so")
 INVDFT_OK, INVDFT_EINVAL, INVDFT_ENOMEM, INVDFT_ECUDA, INVDFT_ENOCONV, INVDFT_ETIMEOUT, \
     INVDFT_ENOTSPD = range(7)
 INVDFT_FP64, INVDFT_MIXED, INVDFT_MIXED_TF32 = 0, 1, 2
+INVDFT_HX_SEG_BALANCED = 0x7fffffff   # seglen of the balanced H~X schedule
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ETIMEOUT",
                 6: "ENOTSPD"}
 

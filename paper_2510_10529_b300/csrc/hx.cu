@@ -312,7 +312,8 @@ bool uses_sweep(const Ctx *c, const HxArgs<T> &a) {
 // Tile variant and z-segment length of the sweep kernel for this launch: the
 // ones fixed by invdft_tune_hx, else the autotuned pair for (precision, ncol,
 // W, E).  The autotuner times every candidate (each tile variant with the
-// whole z range, halves and quarters) on the first such launch of a large
+// whole z range, halves, quarters, segments short enough for two CTAs per SM
+// and the persistent balanced schedule) on the first such launch of a large
 // mesh, writing into the launch's own output, and keeps the fastest; on small
 // meshes, or while the stream is being captured, the defaults are used
 // (variant 0, the whole z range).
@@ -320,7 +321,9 @@ template <typename T>
 std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStream_t s) {
   const int nc = c->g.nc[2], nvar = sweep_variants(c->g, sizeof(T));
   const int fv = c->hx_variant_fixed < nvar ? c->hx_variant_fixed : -1;
-  const int fs = c->hx_seglen_fixed > 0 ? std::min(c->hx_seglen_fixed, nc) : 0;
+  const int fs = c->hx_seglen_fixed == kSegBalanced ? kSegBalanced
+                 : c->hx_seglen_fixed > 0             ? std::min(c->hx_seglen_fixed, nc)
+                                                      : 0;
   if (fv >= 0 && fs > 0) return {fv, fs};
   const long long key = ((long long)a.ncol << 8) | (sizeof(T) << 2) | (a.W ? 2 : 0) | (a.E ? 1 : 0);
   auto it = c->hx_tuned.find(key);
@@ -340,13 +343,15 @@ std::pair<int, int> sweep_config(Ctx *c, const T *v, const HxArgs<T> &a, cudaStr
   }
   std::pair<int, int> best = dflt;
   float best_ms = 1e30f;
-  const int segs[4] = {nc, (nc + 1) / 2, (nc + 3) / 4, par};
+  const int segs[5] = {nc, (nc + 1) / 2, (nc + 3) / 4, par, kSegBalanced};
   for (int var = 0; var < nvar; ++var) {
     if (fv >= 0 && var != fv) continue;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
       const int seg = fs > 0 ? fs : segs[k];
       if (fs > 0 && k > 0) break;
       if (k > 0 && segs[k] == segs[k - 1]) continue;
+      // the balanced schedule exists for the plain epilogue on uniform meshes
+      if (segs[k] == kSegBalanced && (a.W || a.E || c->g.graded)) continue;
       int *err = c->status + kStWaitHxSweep;
       bool ok = launch_hx_sweep(c->g, v, a, err, var, seg, s) == cudaSuccess;
       ok = ok && cudaEventRecord(e0, s) == cudaSuccess;

@@ -38,6 +38,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -148,6 +149,9 @@ struct SweepCoef {
   CT eAx[NE], oAx[NO], eBx[NE], oBx[NO];
   CT eAy[NE], oAy[NO], eBy[NE], oBy[NO];
   CT Az[Q * Q], Bz[Q * Q];
+  // row 0 of the (symmetrised) x and y blocks, for the contribution of the
+  // next cell to a vertex node: applied to the raw values it needs no split
+  CT rAx[Q], rBx[Q], rAy[Q], rBy[Q];
 };
 
 template <typename T, typename CT, int P>
@@ -272,14 +276,11 @@ __device__ __forceinline__ void apply_hi(const V *e1, const V *o1, const CT *eM1
   }
   if (LOC0) *loc0 = vadd(ye[0], yo[0]);
 }
-// row 0 of M u from the halves: sum_k eM[0][k] e_k + sum_k oM[0][k] o_k
+// row 0 of M u from the raw values: sum_k r_k u_k
 template <int P, typename CT, typename V>
-__device__ __forceinline__ V row0(const V *e, const V *o, const CT *eM, const CT *oM, V acc) {
-  constexpr int H = P / 2;
+__device__ __forceinline__ V row0d(const V *u, const CT *r, V acc) {
 #pragma unroll
-  for (int k = 0; k <= H; ++k) acc = vfma(eM[k], e[k], acc);
-#pragma unroll
-  for (int k = 0; k < H; ++k) acc = vfma(oM[k], o[k], acc);
+  for (int k = 0; k <= P; ++k) acc = vfma(r[k], u[k], acc);
   return acc;
 }
 
@@ -287,8 +288,12 @@ __device__ __forceinline__ V row0(const V *e, const V *o, const CT *eM, const CT
 // are the reference blocks; X is scaled by D = d_x d_y d_z as it enters the x
 // sweep, each cell's outputs by its scalars 2/h_e (A) or h_e/2 (B), and the
 // result by D at the output (the nodal term is carried divided by D).
+// BAL: the balanced schedule -- a persistent grid in which every CTA first
+// takes whole (tile, chunk) units round-robin and then an equal share of the
+// z-cells of the units left over; otherwise one (tile, chunk, z segment) item
+// per CTA.
 template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
-          bool HE, bool GR>
+          bool HE, bool GR, bool BAL>
 __global__ void __launch_bounds__(SweepShape<T, P, C, TX, TY, XPT, VW>::NTH, MINB)
 hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::type, P> p,
                 const __grid_constant__ CUtensorMap tmx) {
@@ -313,371 +318,409 @@ hx_sweep_kernel(const __grid_constant__ SweepArgs<T, typename CoefOf<T, VW>::typ
   const SweepCoef<CT, P> &cf = p.cf;
   const int tid = threadIdx.x;
 
-  // work item: (tile, column chunk, z segment)
-  int item = blockIdx.x;
+  // Work: segments (unit, z-cells [n0, n1)), a unit being a (tile, column
+  // chunk) pair numbered tile-fastest.  Per-item launches take one segment
+  // from the block index; the balanced form walks its list.
   const int ntiles = p.ntx * p.nty;
-  const int tile = item % ntiles;
-  item /= ntiles;
-  const int chunk = item % p.nchunk;
-  const int seg = item / p.nchunk;
-  const int gx0 = (tile % p.ntx) * TX, gy0 = (tile / p.ntx) * TY;  // owned index 0, unknown coords
-  const int c0 = chunk * C;
-  const int n0 = seg * p.seglen, n1 = min(p.ncz, n0 + p.seglen);
-  const int gz_begin = n0 == 0 ? 1 : n0 * P;            // node planes (0 = boundary)
-  const int gz_end = n1 * P;
-  const int extra = n1 < p.ncz ? P : 0;
-  const int nplanes = gz_end + extra - gz_begin + 1;
-
-  for (int j = tid; j < C; j += NTH) {
-    const int col = c0 + j;
-    const bool in = col < p.ncol;
-    const double sh = in ? (p.shift_col ? p.shift_col[col] : p.shift) : 0.0;
-    sash[j] = (T)(p.alpha * sh);
-    sesc[j] = (HE && in) ? (T)(p.alpha * p.escale[col]) : (T)0;
+  const int nunit = ntiles * p.nchunk;
+  const int nfull = BAL ? nunit / (int)gridDim.x : 0;            // round-robin whole units
+  int rlo = 0, rhi = 0;                                          // share of the rest, (unit, cell) order
+  if constexpr (BAL) {
+    const long long rest = (long long)(nunit - nfull * (int)gridDim.x) * p.ncz;
+    rlo = (int)(rest * blockIdx.x / gridDim.x);
+    rhi = (int)(rest * (blockIdx.x + 1) / gridDim.x);
   }
-  auto fetch_v = [&](int gzp, int buf) {
-    const int uz = gzp - 1;
-    for (int e = tid; e < TX * TY; e += NTH) {
-      const int lx = e % TX, ly = e / TX;
-      const int vx = gx0 + lx, vy = gy0 + ly;
-      T *dst = &vring[buf][e];
-      if (p.v && uz >= 0 && uz < p.nz && vx < p.nx && vy < p.ny)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
-                     :: "r"(smem_u32(dst)),
-                        "l"(p.v + (size_t)vx + (size_t)p.nx * ((size_t)vy + (size_t)p.ny * uz)),
-                        "n"((int)sizeof(T)) : "memory");
-      else
-        *dst = (T)0;
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  fetch_v(gz_begin, 0);
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < NST; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int s = 0; s < NST && s < nplanes; ++s)
-      load_plane(&tmx, stage0 + s * S::STAGE_STRIDE_V, &full[s], kStageBytes, c0, gx0 - 1,
-                 gy0 - 1, gz_begin + s - 1);
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
-
-  // this thread's y/z task: owned x, a y-cell, a column pair
-  const int cv = tid % NCP;
-  const int ox = (tid / NCP) % TX;
-  const int jy = tid / (NCP * TX);
-  const int ux = gx0 + ox;
-  const int colp = c0 + VW * cv;
-  const bool cx_in = ux < p.nx && colp < p.ncol;
-  const V ash = vload<V>(sash + VW * cv), esc = vload<V>(sesc + VW * cv);
-  const T alpha = (T)p.alpha, beta = (T)p.beta;
-  // graded meshes: D and D^-1 = sqrt(m) of the thread's nodes in x and y
-  T dxy[P], sxy[P];
-  if constexpr (GR) {
-    const int gx = min(ux + 1, p.nx + 1);
-#pragma unroll
-    for (int yi = 0; yi < P; ++yi) {
-      const int gy = min(gy0 + jy * P + yi + 1, p.ny + 1);
-      dxy[yi] = (T)(p.dn[0][gx] * p.dn[1][gy]);
-      sxy[yi] = (T)(p.m1[0][gx] * p.dn[0][gx] * p.m1[1][gy] * p.dn[1][gy]);
-    }
-  }
-  V acc[P + 1][P];
-#pragma unroll
-  for (int i = 0; i <= P; ++i)
-#pragma unroll
-    for (int k = 0; k < P; ++k) acc[i][k] = vzero<V>();
-
-  // store the finished plane g (node numbering) of the thread's nodes
-  auto emit = [&](int g, const V *a) {
-    const int uz = g - 1;
-#pragma unroll
-    for (int yi = 0; yi < P; ++yi) {
-      const int uy = gy0 + jy * P + yi;
-      if (cx_in && uy < p.ny) {
-        const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
-        V val = a[yi];
-        if constexpr (GR) val = vmul((T)(dxy[yi] * p.dn[2][g]), val);
-        // graded meshes add beta W + E here; uniform ones fold them into the
-        // nodal term of their plane
-        if constexpr (HW && GR) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
-        if constexpr (HE && GR) val = vfmav(esc, eload<V>(p.E + off), val);
-        *reinterpret_cast<V *>(p.Z + off) = val;
-      }
-    }
-  };
-
-  // x sweep of one plane: Px = A^x X, Qx = B^x X at the owned x of every row;
-  // a task takes XPT consecutive x-cells of a row (the shared vertices are
-  // summed in registers) and row 0 of the cell after them
-  auto xsweep = [&](const V *xs, V *Pw, V *Qw, int gzp) {
-    const T dz = GR ? (T)p.dn[2][gzp] : (T)1;
-    for (int t = tid; t < S::NTASKX; t += NTH) {
-      const int xcv = t % NCP;
-      const int rest = t / NCP;
-      const int r = rest % RY;
-      const int jt = rest / RY;
-      const V *src = xs + (r * RX + jt * XPT * P) * NCP + xcv;
-      // graded meshes: D of the inputs along this row, and the x-cells' scalars
-      T drow = (T)1;
-      int ex0 = 0;
-      if constexpr (GR) {
-        drow = (T)p.dn[1][min(gy0 + r, p.ny + 1)] * dz;
-        ex0 = gx0 / P + jt * XPT;
-      }
-      auto load_in = [&](V *u, int c) {
-#pragma unroll
-        for (int i = 0; i <= P; ++i) {
-          u[i] = src[(c + i) * NCP];
-          if constexpr (GR)
-            u[i] = vmul((T)(drow * p.dn[0][min(gx0 + jt * XPT * P + c + i, p.nx + 1)]), u[i]);
-        }
-      };
-      V pa[XPT * P], qb[XPT * P];
-#pragma unroll
-      for (int q = 0; q < XPT; ++q) {
-        V u[P + 1], e[H + 1], o[H > 0 ? H : 1];
-        load_in(u, q * P);
-        split<P>(u, e, o);
-        V la, lb;
-        apply_hi<P, false, true>(e, o, cf.eAx, cf.oAx, e, o, cf.eAx, cf.oAx, pa + q * P, &la);
-        apply_hi<P, false, true>(e, o, cf.eBx, cf.oBx, e, o, cf.eBx, cf.oBx, qb + q * P, &lb);
-        if constexpr (GR) {
-          const int ec = min(ex0 + q, p.ncx - 1);
-          const T sa = (T)p.cA[0][ec], sb = (T)p.cB[0][ec];
-#pragma unroll
-          for (int i = 0; i < P; ++i) {
-            pa[q * P + i] = vmul(sa, pa[q * P + i]);
-            qb[q * P + i] = vmul(sb, qb[q * P + i]);
-          }
-          la = vmul(sa, la);
-          lb = vmul(sb, lb);
-        }
-        if (q > 0) {
-          pa[q * P - 1] = vadd(pa[q * P - 1], la);
-          qb[q * P - 1] = vadd(qb[q * P - 1], lb);
-        }
-      }
-      {
-        V u[P + 1], e[H + 1], o[H > 0 ? H : 1];
-        load_in(u, XPT * P);
-        split<P>(u, e, o);
-        if constexpr (GR) {
-          const int ec = min(ex0 + XPT, p.ncx - 1);
-          pa[XPT * P - 1] = vfma((T)p.cA[0][ec], row0<P>(e, o, cf.eAx, cf.oAx, vzero<V>()),
-                                 pa[XPT * P - 1]);
-          qb[XPT * P - 1] = vfma((T)p.cB[0][ec], row0<P>(e, o, cf.eBx, cf.oBx, vzero<V>()),
-                                 qb[XPT * P - 1]);
-        } else {
-          pa[XPT * P - 1] = row0<P>(e, o, cf.eAx, cf.oAx, pa[XPT * P - 1]);
-          qb[XPT * P - 1] = row0<P>(e, o, cf.eBx, cf.oBx, qb[XPT * P - 1]);
-        }
-      }
-      V *dp = Pw + r * PXS + jt * XPT * P * NCP + xcv;
-      V *dq = Qw + r * PXS + jt * XPT * P * NCP + xcv;
-#pragma unroll
-      for (int i = 0; i < XPT * P; ++i) {
-        dp[i * NCP] = pa[i];
-        dq[i * NCP] = qb[i];
-      }
-    }
-  };
-
-  // prologue: x sweep of the first plane
-  if (!wait_parity(&full[0], 0u)) abort_flag = 1;
-  xsweep(stage0, Px, Qx, gz_begin);
-  __syncthreads();
-  // One barrier per plane: the y / z work of plane it (reading Px / Qx buffer
-  // it & 1 and the X stage of plane it) and the x sweep of plane it + 1 (into
-  // the other buffer) run between two barriers.
-  int it = 0;
-  for (; it < nplanes && !abort_flag; ++it) {
-    const int gz = gz_begin + it;
-    const int s = it % NST;
-    const V *stg = stage0 + s * S::STAGE_STRIDE_V;
-    const V *Pr = Px + (it & 1) * 2 * RY * PXS;
-    const V *Qr = Pr + RY * PXS;
-    // potential of the next plane into the other ring slot (its readers
-    // passed the last barrier); this plane's from the ring
-    if (it + 1 < nplanes) fetch_v(gz + 1, (it + 1) & 1);
-    T vv[P];
-#pragma unroll
-    for (int yi = 0; yi < P; ++yi) vv[yi] = vring[it & 1][(jy * P + yi) * TX + ox];
-    // uniform meshes: W and E of this plane at the thread's owned nodes, loaded
-    // here and consumed with the nodal term after the y sweep
-    constexpr bool kFold = (HW || HE) && !GR;
-    V wr[kFold ? P : 1], er[kFold ? P : 1];
-    if constexpr (kFold) {
-      const int uz = gz - 1;
-      const bool own = gz > n0 * P && gz <= gz_end && uz < p.nz;
-#pragma unroll
-      for (int yi = 0; yi < P; ++yi) {
-        const int uy = gy0 + jy * P + yi;
-        wr[yi] = vzero<V>();
-        er[yi] = vzero<V>();
-        if (own && cx_in && uy < p.ny) {
-          const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
-          if constexpr (HW) wr[yi] = *reinterpret_cast<const V *>(p.W + off);
-          if constexpr (HE) er[yi] = eload<V>(p.E + off);
-        }
-      }
-    }
-
-    // ---- y sweep: R = B^y Px + A^y Qx, S = B^y Qx at this thread's p nodes
-    V R[P], Sv[P];
-    {
-      const V *sp = Pr + jy * P * PXS + ox * NCP + cv;
-      const V *sq = Qr + jy * P * PXS + ox * NCP + cv;
-      V u[P + 1], w[P + 1], eu[H + 1], ou[H > 0 ? H : 1], ew[H + 1], ow[H > 0 ? H : 1];
-#pragma unroll
-      for (int i = 0; i <= P; ++i) {
-        u[i] = sp[i * PXS];
-        w[i] = sq[i * PXS];
-      }
-      split<P>(u, eu, ou);
-      split<P>(w, ew, ow);
-      if constexpr (GR) {
-        // R = s_B B Px + s_A A Qx, S = s_B B Qx with the y-cell's scalars
-        const int ey = min((gy0 + jy * P) / P, p.ncy - 1);
-        const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
-        V Ra[P], Rb[P];
-        apply_hi<P, false, false>(eu, ou, cf.eBy, cf.oBy, eu, ou, cf.eBy, cf.oBy, Rb, Rb);
-        apply_hi<P, false, false>(ew, ow, cf.eAy, cf.oAy, ew, ow, cf.eAy, cf.oAy, Ra, Ra);
-        apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          R[i] = vfma(sb, Rb[i], vmul(sa, Ra[i]));
-          Sv[i] = vmul(sb, Sv[i]);
-        }
-      } else {
-        apply_hi<P, true, false>(eu, ou, cf.eBy, cf.oBy, ew, ow, cf.eAy, cf.oAy, R, R);
-        apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
-      }
-#pragma unroll
-      for (int i = 0; i <= P; ++i) {
-        u[i] = sp[(P + i) * PXS];
-        w[i] = sq[(P + i) * PXS];
-      }
-      split<P>(u, eu, ou);
-      split<P>(w, ew, ow);
-      if constexpr (GR) {
-        const int ey = min((gy0 + jy * P) / P + 1, p.ncy - 1);
-        const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
-        R[P - 1] = vfma(sb, row0<P>(eu, ou, cf.eBy, cf.oBy, vzero<V>()), R[P - 1]);
-        R[P - 1] = vfma(sa, row0<P>(ew, ow, cf.eAy, cf.oAy, vzero<V>()), R[P - 1]);
-        Sv[P - 1] = vfma(sb, row0<P>(ew, ow, cf.eBy, cf.oBy, vzero<V>()), Sv[P - 1]);
-      } else {
-        R[P - 1] = row0<P>(ew, ow, cf.eAy, cf.oAy, row0<P>(eu, ou, cf.eBy, cf.oBy, R[P - 1]));
-        Sv[P - 1] = row0<P>(ew, ow, cf.eBy, cf.oBy, Sv[P - 1]);
-      }
-    }
-    // nodal term of this plane at the thread's nodes: alpha (v - shift_j) X_j
-    V nod[P];
-#pragma unroll
-    for (int yi = 0; yi < P; ++yi) {
-      const int oy = jy * P + yi;
-      const V xv = stg[((oy + 1) * RX + ox + 1) * NCP + cv];
-      nod[yi] = vfmav(vrsub(alpha * vv[yi], ash), xv, vzero<V>());
-      // graded meshes: carried divided by D (restored at the output)
-      if constexpr (GR) nod[yi] = vmul((T)(sxy[yi] * p.m1[2][gz] * p.dn[2][gz]), nod[yi]);
-      if constexpr (kFold && HW) nod[yi] = vfma(beta, wr[yi], nod[yi]);
-      if constexpr (kFold && HE) nod[yi] = vfmav(esc, er[yi], nod[yi]);
-    }
-
-    // ---- z: accumulate the planes of the current z-cell
-    const int n = gz / P, kz = gz - n * P;
-    // graded meshes: R, S of this plane scaled by the z-cell's scalars (the
-    // vertex plane belongs to two cells)
-    V Rz[P], Sz[P];
-    auto zscale = [&](int cell) {
-      if constexpr (GR) {
-        const int ec = min(cell, p.ncz - 1);
-        const T sb = (T)p.cB[2][ec], sa = (T)p.cA[2][ec];
-#pragma unroll
-        for (int yi = 0; yi < P; ++yi) {
-          Rz[yi] = vmul(sb, R[yi]);
-          Sz[yi] = vmul(sa, Sv[yi]);
-        }
-      }
-    };
-    const V *Ru = GR ? Rz : R, *Su = GR ? Sz : Sv;
-    auto zall = [&](int k) {
-#pragma unroll
-      for (int i = 0; i <= P; ++i) {
-        const CT b = cf.Bz[i * (P + 1) + k], a = cf.Az[i * (P + 1) + k];
-#pragma unroll
-        for (int yi = 0; yi < P; ++yi) acc[i][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[i][yi]));
-      }
-    };
-    auto zrow0 = [&](int k) {
-      const CT b = cf.Bz[k], a = cf.Az[k];
-#pragma unroll
-      for (int yi = 0; yi < P; ++yi) acc[0][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[0][yi]));
-    };
-    if (gz <= gz_end) {
-      if (kz == 0 && gz > n0 * P) {
-        // vertex plane: close cell n-1, write its planes, carry the vertex
-        zscale(n - 1);
-        zall(P);
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          const int g = (n - 1) * P + i;
-          if (g > n0 * P) emit(g, acc[i]);
-        }
-#pragma unroll
-        for (int yi = 0; yi < P; ++yi) {
-          acc[0][yi] = vadd(acc[P][yi], nod[yi]);
-#pragma unroll
-          for (int i = 1; i <= P; ++i) acc[i][yi] = vzero<V>();
-        }
-        zscale(n);
-        if (gz < gz_end) zall(0);
-        else if (extra) zrow0(0);
-      } else if (kz == 0) {
-        zscale(n);
-        zall(0);                      // bottom vertex of a segment: not owned here
-      } else {
-        zscale(n);
-        zall(kz);
-#pragma unroll
-        for (int i = 1; i < P; ++i)
-          if (i == kz) {
-#pragma unroll
-            for (int yi = 0; yi < P; ++yi) acc[i][yi] = vadd(acc[i][yi], nod[yi]);
-          }
-      }
+  // planes consumed by earlier segments: plane it of this segment is the
+  // (gbase + it)-th load of the CTA, in stage (gbase + it) % NST, and its wait
+  // parity is ((gbase + it) / NST) & 1
+  int gbase = 0;
+  int it = 0, nplanes = 0;
+  for (int kseg = 0; BAL ? !abort_flag : kseg == 0; ++kseg) {
+    int unit, n0, n1;
+    if constexpr (!BAL) {
+      int item = blockIdx.x;
+      unit = item % ntiles;
+      item /= ntiles;
+      unit += ntiles * (item % p.nchunk);
+      n0 = (item / p.nchunk) * p.seglen;
+      n1 = min(p.ncz, n0 + p.seglen);
+    } else if (kseg < nfull) {
+      unit = blockIdx.x + kseg * gridDim.x;
+      n0 = 0;
+      n1 = p.ncz;
     } else {
-      // planes above the top vertex of the segment: row 0 of the next cell
-      const int kk = gz - gz_end;
-      zscale(n1);
-      zrow0(kk);
-      if (kk == P) emit(gz_end, acc[0]);
+      if (rlo >= rhi) break;
+      unit = nfull * gridDim.x + rlo / p.ncz;
+      n0 = rlo % p.ncz;
+      n1 = min(p.ncz, n0 + (rhi - rlo));
+      rlo += n1 - n0;
     }
-    // x sweep of the next plane into the other buffer
-    if (it + 1 < nplanes) {
-      const int s1 = (it + 1) % NST;
-      if (!wait_parity(&full[s1], (uint32_t)(((it + 1) / NST) & 1))) abort_flag = 1;
-      V *Pw = Px + ((it + 1) & 1) * 2 * RY * PXS;
-      xsweep(stage0 + s1 * S::STAGE_STRIDE_V, Pw, Pw + RY * PXS, gz + 1);
+    const int tile = unit % ntiles, chunk = unit / ntiles;
+    const int gx0 = (tile % p.ntx) * TX, gy0 = (tile / p.ntx) * TY;  // owned index 0, unknown coords
+    const int c0 = chunk * C;
+    const int gz_begin = n0 == 0 ? 1 : n0 * P;            // node planes (0 = boundary)
+    const int gz_end = n1 * P;
+    const int extra = n1 < p.ncz ? P : 0;
+    nplanes = gz_end + extra - gz_begin + 1;
+
+    for (int j = tid; j < C; j += NTH) {
+      const int col = c0 + j;
+      const bool in = col < p.ncol;
+      const double sh = in ? (p.shift_col ? p.shift_col[col] : p.shift) : 0.0;
+      sash[j] = (T)(p.alpha * sh);
+      sesc[j] = (HE && in) ? (T)(p.alpha * p.escale[col]) : (T)0;
+    }
+    auto fetch_v = [&](int gzp, int buf) {
+      const int uz = gzp - 1;
+      for (int e = tid; e < TX * TY; e += NTH) {
+        const int lx = e % TX, ly = e / TX;
+        const int vx = gx0 + lx, vy = gy0 + ly;
+        T *dst = &vring[buf][e];
+        if (p.v && uz >= 0 && uz < p.nz && vx < p.nx && vy < p.ny)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;"
+                       :: "r"(smem_u32(dst)),
+                          "l"(p.v + (size_t)vx + (size_t)p.nx * ((size_t)vy + (size_t)p.ny * uz)),
+                          "n"((int)sizeof(T)) : "memory");
+        else
+          *dst = (T)0;
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    fetch_v(gz_begin, 0);
+    if (tid == 0) {
+      // every stage is free: the previous segment's readers passed its last barrier
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int s = 0; s < NST && s < nplanes; ++s) {
+        const int st = (gbase + s) % NST;
+        load_plane(&tmx, stage0 + st * S::STAGE_STRIDE_V, &full[st], kStageBytes, c0, gx0 - 1,
+                   gy0 - 1, gz_begin + s - 1);
+      }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    // the stage of plane it is free: fetch the plane NST ahead into it
-    if (tid == 0 && it + NST < nplanes) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      load_plane(&tmx, stage0 + s * S::STAGE_STRIDE_V, &full[s], kStageBytes, c0, gx0 - 1,
-                 gy0 - 1, gz + NST - 1);
+
+    // this thread's y/z task: owned x, a y-cell, a column pair
+    const int cv = tid % NCP;
+    const int ox = (tid / NCP) % TX;
+    const int jy = tid / (NCP * TX);
+    const int ux = gx0 + ox;
+    const int colp = c0 + VW * cv;
+    const bool cx_in = ux < p.nx && colp < p.ncol;
+    const V ash = vload<V>(sash + VW * cv), esc = vload<V>(sesc + VW * cv);
+    const T alpha = (T)p.alpha, beta = (T)p.beta;
+    // graded meshes: D and D^-1 = sqrt(m) of the thread's nodes in x and y
+    T dxy[P], sxy[P];
+    if constexpr (GR) {
+      const int gx = min(ux + 1, p.nx + 1);
+#pragma unroll
+      for (int yi = 0; yi < P; ++yi) {
+        const int gy = min(gy0 + jy * P + yi + 1, p.ny + 1);
+        dxy[yi] = (T)(p.dn[0][gx] * p.dn[1][gy]);
+        sxy[yi] = (T)(p.m1[0][gx] * p.dn[0][gx] * p.m1[1][gy] * p.dn[1][gy]);
+      }
     }
-  }
+    V acc[P + 1][P];
+#pragma unroll
+    for (int i = 0; i <= P; ++i)
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc[i][k] = vzero<V>();
+
+    // store the finished plane g (node numbering) of the thread's nodes
+    auto emit = [&](int g, const V *a) {
+      const int uz = g - 1;
+#pragma unroll
+      for (int yi = 0; yi < P; ++yi) {
+        const int uy = gy0 + jy * P + yi;
+        if (cx_in && uy < p.ny) {
+          const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
+          V val = a[yi];
+          if constexpr (GR) val = vmul((T)(dxy[yi] * p.dn[2][g]), val);
+          // graded meshes add beta W + E here; uniform ones fold them into the
+          // nodal term of their plane
+          if constexpr (HW && GR) val = vfma(beta, *reinterpret_cast<const V *>(p.W + off), val);
+          if constexpr (HE && GR) val = vfmav(esc, eload<V>(p.E + off), val);
+          *reinterpret_cast<V *>(p.Z + off) = val;
+        }
+      }
+    };
+
+    // x sweep of one plane: Px = A^x X, Qx = B^x X at the owned x of every row;
+    // a task takes XPT consecutive x-cells of a row (the shared vertices are
+    // summed in registers) and row 0 of the cell after them
+    auto xsweep = [&](const V *xs, V *Pw, V *Qw, int gzp) {
+      const T dz = GR ? (T)p.dn[2][gzp] : (T)1;
+      for (int t = tid; t < S::NTASKX; t += NTH) {
+        const int xcv = t % NCP;
+        const int rest = t / NCP;
+        const int r = rest % RY;
+        const int jt = rest / RY;
+        const V *src = xs + (r * RX + jt * XPT * P) * NCP + xcv;
+        // graded meshes: D of the inputs along this row, and the x-cells' scalars
+        T drow = (T)1;
+        int ex0 = 0;
+        if constexpr (GR) {
+          drow = (T)p.dn[1][min(gy0 + r, p.ny + 1)] * dz;
+          ex0 = gx0 / P + jt * XPT;
+        }
+        auto load_in = [&](V *u, int c) {
+#pragma unroll
+          for (int i = 0; i <= P; ++i) {
+            u[i] = src[(c + i) * NCP];
+            if constexpr (GR)
+              u[i] = vmul((T)(drow * p.dn[0][min(gx0 + jt * XPT * P + c + i, p.nx + 1)]), u[i]);
+          }
+        };
+        V pa[XPT * P], qb[XPT * P];
+#pragma unroll
+        for (int q = 0; q < XPT; ++q) {
+          V u[P + 1], e[H + 1], o[H > 0 ? H : 1];
+          load_in(u, q * P);
+          split<P>(u, e, o);
+          V la, lb;
+          apply_hi<P, false, true>(e, o, cf.eAx, cf.oAx, e, o, cf.eAx, cf.oAx, pa + q * P, &la);
+          apply_hi<P, false, true>(e, o, cf.eBx, cf.oBx, e, o, cf.eBx, cf.oBx, qb + q * P, &lb);
+          if constexpr (GR) {
+            const int ec = min(ex0 + q, p.ncx - 1);
+            const T sa = (T)p.cA[0][ec], sb = (T)p.cB[0][ec];
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+              pa[q * P + i] = vmul(sa, pa[q * P + i]);
+              qb[q * P + i] = vmul(sb, qb[q * P + i]);
+            }
+            la = vmul(sa, la);
+            lb = vmul(sb, lb);
+          }
+          if (q > 0) {
+            pa[q * P - 1] = vadd(pa[q * P - 1], la);
+            qb[q * P - 1] = vadd(qb[q * P - 1], lb);
+          }
+        }
+        {
+          V u[P + 1];
+          load_in(u, XPT * P);
+          if constexpr (GR) {
+            const int ec = min(ex0 + XPT, p.ncx - 1);
+            pa[XPT * P - 1] = vfma((T)p.cA[0][ec], row0d<P>(u, cf.rAx, vzero<V>()), pa[XPT * P - 1]);
+            qb[XPT * P - 1] = vfma((T)p.cB[0][ec], row0d<P>(u, cf.rBx, vzero<V>()), qb[XPT * P - 1]);
+          } else {
+            pa[XPT * P - 1] = row0d<P>(u, cf.rAx, pa[XPT * P - 1]);
+            qb[XPT * P - 1] = row0d<P>(u, cf.rBx, qb[XPT * P - 1]);
+          }
+        }
+        V *dp = Pw + r * PXS + jt * XPT * P * NCP + xcv;
+        V *dq = Qw + r * PXS + jt * XPT * P * NCP + xcv;
+#pragma unroll
+        for (int i = 0; i < XPT * P; ++i) {
+          dp[i * NCP] = pa[i];
+          dq[i * NCP] = qb[i];
+        }
+      }
+    };
+
+    // prologue: x sweep of the first plane
+    {
+      const int st = gbase % NST;
+      if (!wait_parity(&full[st], (uint32_t)((gbase / NST) & 1))) abort_flag = 1;
+      xsweep(stage0 + st * S::STAGE_STRIDE_V, Px, Qx, gz_begin);
+    }
+    __syncthreads();
+    // One barrier per plane: the y / z work of plane it (reading Px / Qx buffer
+    // it & 1 and the X stage of plane it) and the x sweep of plane it + 1 (into
+    // the other buffer) run between two barriers.
+    for (it = 0; it < nplanes && !abort_flag; ++it) {
+      const int gz = gz_begin + it;
+      const int s = (gbase + it) % NST;
+      const V *stg = stage0 + s * S::STAGE_STRIDE_V;
+      const V *Pr = Px + (it & 1) * 2 * RY * PXS;
+      const V *Qr = Pr + RY * PXS;
+      // potential of the next plane into the other ring slot (its readers
+      // passed the last barrier); this plane's from the ring
+      if (it + 1 < nplanes) fetch_v(gz + 1, (it + 1) & 1);
+      T vv[P];
+#pragma unroll
+      for (int yi = 0; yi < P; ++yi) vv[yi] = vring[it & 1][(jy * P + yi) * TX + ox];
+      // uniform meshes: W and E of this plane at the thread's owned nodes, loaded
+      // here and consumed with the nodal term after the y sweep
+      constexpr bool kFold = (HW || HE) && !GR;
+      V wr[kFold ? P : 1], er[kFold ? P : 1];
+      if constexpr (kFold) {
+        const int uz = gz - 1;
+        const bool own = gz > n0 * P && gz <= gz_end && uz < p.nz;
+#pragma unroll
+        for (int yi = 0; yi < P; ++yi) {
+          const int uy = gy0 + jy * P + yi;
+          wr[yi] = vzero<V>();
+          er[yi] = vzero<V>();
+          if (own && cx_in && uy < p.ny) {
+            const size_t off = ((size_t)ux + (size_t)p.nx * ((size_t)uy + (size_t)p.ny * uz)) * p.ncol + colp;
+            if constexpr (HW) wr[yi] = *reinterpret_cast<const V *>(p.W + off);
+            if constexpr (HE) er[yi] = eload<V>(p.E + off);
+          }
+        }
+      }
+
+      // ---- y sweep: R = B^y Px + A^y Qx, S = B^y Qx at this thread's p nodes
+      V R[P], Sv[P];
+      {
+        const V *sp = Pr + jy * P * PXS + ox * NCP + cv;
+        const V *sq = Qr + jy * P * PXS + ox * NCP + cv;
+        V u[P + 1], w[P + 1], eu[H + 1], ou[H > 0 ? H : 1], ew[H + 1], ow[H > 0 ? H : 1];
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+          u[i] = sp[i * PXS];
+          w[i] = sq[i * PXS];
+        }
+        split<P>(u, eu, ou);
+        split<P>(w, ew, ow);
+        if constexpr (GR) {
+          // R = s_B B Px + s_A A Qx, S = s_B B Qx with the y-cell's scalars
+          const int ey = min((gy0 + jy * P) / P, p.ncy - 1);
+          const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
+          V Ra[P], Rb[P];
+          apply_hi<P, false, false>(eu, ou, cf.eBy, cf.oBy, eu, ou, cf.eBy, cf.oBy, Rb, Rb);
+          apply_hi<P, false, false>(ew, ow, cf.eAy, cf.oAy, ew, ow, cf.eAy, cf.oAy, Ra, Ra);
+          apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            R[i] = vfma(sb, Rb[i], vmul(sa, Ra[i]));
+            Sv[i] = vmul(sb, Sv[i]);
+          }
+        } else {
+          apply_hi<P, true, false>(eu, ou, cf.eBy, cf.oBy, ew, ow, cf.eAy, cf.oAy, R, R);
+          apply_hi<P, false, false>(ew, ow, cf.eBy, cf.oBy, ew, ow, cf.eBy, cf.oBy, Sv, Sv);
+        }
+        // row 0 of the next y-cell
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+          u[i] = sp[(P + i) * PXS];
+          w[i] = sq[(P + i) * PXS];
+        }
+        if constexpr (GR) {
+          const int ey = min((gy0 + jy * P) / P + 1, p.ncy - 1);
+          const T sa = (T)p.cA[1][ey], sb = (T)p.cB[1][ey];
+          R[P - 1] = vfma(sb, row0d<P>(u, cf.rBy, vzero<V>()), R[P - 1]);
+          R[P - 1] = vfma(sa, row0d<P>(w, cf.rAy, vzero<V>()), R[P - 1]);
+          Sv[P - 1] = vfma(sb, row0d<P>(w, cf.rBy, vzero<V>()), Sv[P - 1]);
+        } else {
+          R[P - 1] = row0d<P>(w, cf.rAy, row0d<P>(u, cf.rBy, R[P - 1]));
+          Sv[P - 1] = row0d<P>(w, cf.rBy, Sv[P - 1]);
+        }
+      }
+      // nodal term of this plane at the thread's nodes: alpha (v - shift_j) X_j
+      V nod[P];
+#pragma unroll
+      for (int yi = 0; yi < P; ++yi) {
+        const int oy = jy * P + yi;
+        const V xv = stg[((oy + 1) * RX + ox + 1) * NCP + cv];
+        nod[yi] = vfmav(vrsub(alpha * vv[yi], ash), xv, vzero<V>());
+        // graded meshes: carried divided by D (restored at the output)
+        if constexpr (GR) nod[yi] = vmul((T)(sxy[yi] * p.m1[2][gz] * p.dn[2][gz]), nod[yi]);
+        if constexpr (kFold && HW) nod[yi] = vfma(beta, wr[yi], nod[yi]);
+        if constexpr (kFold && HE) nod[yi] = vfmav(esc, er[yi], nod[yi]);
+      }
+
+      // ---- z: accumulate the planes of the current z-cell
+      const int n = gz / P, kz = gz - n * P;
+      // graded meshes: R, S of this plane scaled by the z-cell's scalars (the
+      // vertex plane belongs to two cells)
+      V Rz[P], Sz[P];
+      auto zscale = [&](int cell) {
+        if constexpr (GR) {
+          const int ec = min(cell, p.ncz - 1);
+          const T sb = (T)p.cB[2][ec], sa = (T)p.cA[2][ec];
+#pragma unroll
+          for (int yi = 0; yi < P; ++yi) {
+            Rz[yi] = vmul(sb, R[yi]);
+            Sz[yi] = vmul(sa, Sv[yi]);
+          }
+        }
+      };
+      const V *Ru = GR ? Rz : R, *Su = GR ? Sz : Sv;
+      auto zall = [&](int k) {
+#pragma unroll
+        for (int i = 0; i <= P; ++i) {
+          const CT b = cf.Bz[i * (P + 1) + k], a = cf.Az[i * (P + 1) + k];
+#pragma unroll
+          for (int yi = 0; yi < P; ++yi) acc[i][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[i][yi]));
+        }
+      };
+      auto zrow0 = [&](int k) {
+        const CT b = cf.Bz[k], a = cf.Az[k];
+#pragma unroll
+        for (int yi = 0; yi < P; ++yi) acc[0][yi] = vfma(b, Ru[yi], vfma(a, Su[yi], acc[0][yi]));
+      };
+      if (gz <= gz_end) {
+        if (kz == 0 && gz > n0 * P) {
+          // vertex plane: close cell n-1, write its planes, carry the vertex
+          zscale(n - 1);
+          zall(P);
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const int g = (n - 1) * P + i;
+            if (g > n0 * P) emit(g, acc[i]);
+          }
+#pragma unroll
+          for (int yi = 0; yi < P; ++yi) {
+            acc[0][yi] = vadd(acc[P][yi], nod[yi]);
+#pragma unroll
+            for (int i = 1; i <= P; ++i) acc[i][yi] = vzero<V>();
+          }
+          zscale(n);
+          if (gz < gz_end) zall(0);
+          else if (extra) zrow0(0);
+        } else if (kz == 0) {
+          zscale(n);
+          zall(0);                      // bottom vertex of a segment: not owned here
+        } else {
+          zscale(n);
+          zall(kz);
+#pragma unroll
+          for (int i = 1; i < P; ++i)
+            if (i == kz) {
+#pragma unroll
+              for (int yi = 0; yi < P; ++yi) acc[i][yi] = vadd(acc[i][yi], nod[yi]);
+            }
+        }
+      } else {
+        // planes above the top vertex of the segment: row 0 of the next cell
+        const int kk = gz - gz_end;
+        zscale(n1);
+        zrow0(kk);
+        if (kk == P) emit(gz_end, acc[0]);
+      }
+      // x sweep of the next plane into the other buffer
+      if (it + 1 < nplanes) {
+        const int s1 = (gbase + it + 1) % NST;
+        if (!wait_parity(&full[s1], (uint32_t)(((gbase + it + 1) / NST) & 1))) abort_flag = 1;
+        V *Pw = Px + ((it + 1) & 1) * 2 * RY * PXS;
+        xsweep(stage0 + s1 * S::STAGE_STRIDE_V, Pw, Pw + RY * PXS, gz + 1);
+      }
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+      // the stage of plane it is free: fetch the plane NST ahead into it
+      if (tid == 0 && it + NST < nplanes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        load_plane(&tmx, stage0 + s * S::STAGE_STRIDE_V, &full[s], kStageBytes, c0, gx0 - 1,
+                   gy0 - 1, gz + NST - 1);
+      }
+    }
+    if (abort_flag) break;
+    gbase += nplanes;
+  }  // segments
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (abort_flag && tid == 0) {
     // a plane never arrived: report, and give the loads still in flight a
     // bounded chance to land before the CTA's shared memory is released
     atomicExch(p.err, 3);
     for (int k = it; k < nplanes && k < it + NST; ++k)
-      wait_parity(&full[k % NST], (uint32_t)((k / NST) & 1));
+      wait_parity(&full[(gbase + k) % NST], (uint32_t)(((gbase + k) / NST) & 1));
   }
 }
 
@@ -710,6 +753,12 @@ void scaled_blocks(const Geom &g, int axis, double *Ah, double *Bh) {
       Bh[i * Q + j] = di * (g.B[i * Q + j] * s) * dj;
     }
 }
+// row 0 of a centrosymmetric matrix (symmetrised as in eo_blocks)
+template <int P, typename T, int VW, typename CT>
+void row0_block(const double *M, CT *r) {
+  constexpr int Q = P + 1;
+  for (int k = 0; k < Q; ++k) r[k] = CoefOf<T, VW>::make(0.5 * (M[k] + M[P * Q + (P - k)]));
+}
 // even / odd blocks of a centrosymmetric matrix (symmetrised first)
 template <int P, typename T, int VW, typename CT>
 void eo_blocks(const double *M, CT *e, CT *o) {
@@ -738,6 +787,10 @@ void make_coef(const Geom &g, double alpha, bool graded, SweepCoef<CT, P> *cf) {
     eo_blocks<P, T, VW>(Bh, cf->eBx, cf->oBx);
     eo_blocks<P, T, VW>(Ah, cf->eAy, cf->oAy);
     eo_blocks<P, T, VW>(Bh, cf->eBy, cf->oBy);
+    row0_block<P, T, VW>(Ah, cf->rAx);
+    row0_block<P, T, VW>(Bh, cf->rBx);
+    row0_block<P, T, VW>(Ah, cf->rAy);
+    row0_block<P, T, VW>(Bh, cf->rBy);
     for (int i = 0; i < Q * Q; ++i) {
       cf->Az[i] = CoefOf<T, VW>::make(0.5 * alpha * Ah[i]);
       cf->Bz[i] = CoefOf<T, VW>::make(0.5 * alpha * Bh[i]);
@@ -747,9 +800,13 @@ void make_coef(const Geom &g, double alpha, bool graded, SweepCoef<CT, P> *cf) {
   scaled_blocks<P>(g, 0, Ah, Bh);
   eo_blocks<P, T, VW>(Ah, cf->eAx, cf->oAx);
   eo_blocks<P, T, VW>(Bh, cf->eBx, cf->oBx);
+  row0_block<P, T, VW>(Ah, cf->rAx);
+  row0_block<P, T, VW>(Bh, cf->rBx);
   scaled_blocks<P>(g, 1, Ah, Bh);
   eo_blocks<P, T, VW>(Ah, cf->eAy, cf->oAy);
   eo_blocks<P, T, VW>(Bh, cf->eBy, cf->oBy);
+  row0_block<P, T, VW>(Ah, cf->rAy);
+  row0_block<P, T, VW>(Bh, cf->rBy);
   scaled_blocks<P>(g, 2, Ah, Bh);
   for (int i = 0; i < Q * Q; ++i) {
     cf->Az[i] = CoefOf<T, VW>::make(0.5 * alpha * Ah[i]);
@@ -757,17 +814,40 @@ void make_coef(const Geom &g, double alpha, bool graded, SweepCoef<CT, P> *cf) {
   }
 }
 
+// CTAs of kernel k (nth threads, smem bytes) resident on the current device
+// at once; cached per device (the shared-memory limit is raised before)
+template <typename K>
+int resident_grid(K *k, int nth, size_t smem) {
+  static std::atomic<int> cache[16];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev < 16 && cache[dev].load() > 0) return cache[dev].load();
+  int nsm = 0, occ = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nth, smem) != cudaSuccess)
+    return 0;
+  const int g = nsm * std::max(occ, 1);
+  if (dev < 16) cache[dev].store(g);
+  return g;
+}
+
 template <typename T, int P, int C, int TX, int TY, int NST, int XPT, int MINB, int VW, bool HW,
-          bool HE, bool GR>
+          bool HE, bool GR, bool BAL = false>
 cudaError_t run_sweep(const SweepArgs<T, typename CoefOf<T, VW>::type, P> &a, const CUtensorMap &tm,
                       int nitems, cudaStream_t s) {
   using Sh = SweepShape<T, P, C, TX, TY, XPT, VW>;
-  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, VW, HW, HE, GR>;
+  auto k = hx_sweep_kernel<T, P, C, TX, TY, NST, XPT, MINB, VW, HW, HE, GR, BAL>;
   const size_t smem = Sh::smem(NST);
   cudaError_t e = raise_smem_limit(k, smem);
   if (e != cudaSuccess) return e;
+  int grid = nitems;
+  if (BAL) {
+    // the persistent form: one CTA per resident slot
+    grid = resident_grid(k, Sh::NTH, smem);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+  }
   ::invdft::count_launch();
-  k<<<nitems, Sh::NTH, smem, s>>>(a, tm);
+  k<<<grid, Sh::NTH, smem, s>>>(a, tm);
   return cudaGetLastError();
 }
 
@@ -806,6 +886,11 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   sa.ntx = (g.n[0] + TX - 1) / TX;
   sa.nty = (g.n[1] + TY - 1) / TY;
   sa.nchunk = (a.ncol + C - 1) / C;
+  // the balanced schedule is built for the plain epilogue on uniform meshes
+  // (the operator and the MINRES iterations); other launches with it fixed
+  // run the whole z range per CTA
+  const bool bal = seglen == kSegBalanced && !a.W && !a.E && !GR;
+  if (seglen == kSegBalanced) seglen = g.nc[2];
   if (seglen < 0) {
     // the segment length that gives at least -seglen work items (CTAs)
     const long long per = (long long)sa.ntx * sa.nty * sa.nchunk;
@@ -834,6 +919,9 @@ cudaError_t sweep_variant(const Geom &g, const T *v, const HxArgs<T> &a, int *er
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const bool hw = a.W != nullptr, he = a.E != nullptr;
   const int n = (int)nitems;
+  if constexpr (!GR) {
+    if (bal) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, false, GR, true>(sa, tm, n, s);
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (hw && he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, true, true, GR>(sa, tm, n, s);
     if (he) return run_sweep<T, P, C, TX, TY, NST, XPT, MINB, VW, false, true, GR>(sa, tm, n, s);

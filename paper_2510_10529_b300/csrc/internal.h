@@ -275,10 +275,15 @@ void build_cell_order(int nc, std::vector<int> *perm);
 // the final wait gave up; flops: the launch's floating-point operations
 cudaError_t launch_tf32_probe(int grid, int chains, int *err, double *flops, cudaStream_t s);
 // Owner-computes sweep form of H~X (hx_sweep.cu): FP32 and FP64 blocks on
-// orders 2 and 4, ncol * elem a multiple of 16 bytes, 16-byte aligned blocks,
-// Z not aliasing X, W or E.  variant in [0, sweep_variants) selects the tile
-// shape; seglen = z-cells per CTA (the z range is split into segments of that
-// many cells).  err: device word set to 3 if a wait for a TMA plane gave up.
+// orders 2, 4 and 6, ncol * elem a multiple of 16 bytes, 16-byte aligned
+// blocks, Z not aliasing X, W or E.  variant in [0, sweep_variants) selects the
+// tile shape; seglen = z-cells per CTA (the z range is split into segments of
+// that many cells), or kSegBalanced for the persistent balanced schedule (one
+// CTA per resident slot: whole (tile, chunk) units round-robin, then an equal
+// share of the z-cells of the units left over; plain launches on uniform
+// meshes, others run the whole z range).  err: device word set to 3 if a wait
+// for a TMA plane gave up.
+constexpr int kSegBalanced = INVDFT_HX_SEG_BALANCED;
 bool sweep_supported(const Geom &g, int ncol, size_t elem, const void *X, const void *Z,
                      const void *W, const void *E);
 int sweep_variants(const Geom &g, size_t elem);

@@ -6,8 +6,10 @@ The sweep kernel runs every FP32 and FP64 block whose rows are a multiple of
 16 bytes on Q2 and Q4 meshes.  The cases below cover: tiles that overhang the
 mesh edge (unknowns per axis not a multiple of the tile), several column
 chunks with a ragged last chunk (36 FP32 columns = 16 + 16 + 4), z segments of
-one cell (every cell has a segment top vertex and extra planes), two cells and
-the whole range, and the Chebyshev filter's W epilogue.  Tolerances as in
+one cell (every cell has a segment top vertex and extra planes), two cells, the
+whole range and the balanced persistent schedule (CTAs that take several
+segments of different units; launches with the filter's W epilogue fall back
+to the whole range under it), and the Chebyshev filter's W epilogue.  Tolerances as in
 test_gpu_parity: FP64 1e-10, FP32 2e-6 (max over columns of the relative
 2-norm error).
 """
@@ -33,8 +35,11 @@ def _colrel(Yg, Yo):
 MESHES = [(-5.0, 5.0, 5, 2), (-4.0, 5.0, 3, 4), (-6.0, 6.0, 5, 4)]
 
 
+BALANCED = 0x7fffffff   # INVDFT_HX_SEG_BALANCED: the persistent balanced schedule
+
+
 @pytest.mark.parametrize("geom", MESHES)
-@pytest.mark.parametrize("seglen", [1, 2, 0])
+@pytest.mark.parametrize("seglen", [1, 2, 0, BALANCED])
 @pytest.mark.parametrize("dtype,ncols,tol", [(torch.float64, (2, 6, 18), 1e-10),
                                              (torch.float32, (4, 12, 36, 64), 2e-6)])
 def test_sweep_apply_h_matches_oracle(geom, seglen, dtype, ncols, tol):
@@ -60,7 +65,7 @@ def test_sweep_apply_h_matches_oracle(geom, seglen, dtype, ncols, tol):
             assert err <= tol
 
 
-@pytest.mark.parametrize("seglen", [1, 3])
+@pytest.mark.parametrize("seglen", [1, 3, BALANCED])
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-9), (torch.float32, 2e-5)])
 def test_sweep_filter_epilogue_matches_oracle(seglen, dtype, tol):
     """The filter's three-term recurrence, Z = alpha (H~ - c) X + beta W, on
@@ -111,3 +116,42 @@ def test_every_variant_in_the_defect_corrected_filter(ncell, order):
         print(f"defect filter p={order} variant={variant}: deps={deps:.2e} drho={drho:.2e}")
         assert deps <= 1e-6
         assert drho <= 1e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, 2e-6), (torch.float64, 1e-10)])
+def test_balanced_schedule_full_size(dtype, tol):
+    """The balanced schedule on the 32^3-cell Q4 operator benchmark (2,048,383
+    unknowns, 64 columns), every tile variant: each CTA takes one whole unit
+    and then about 23 z-cells of the units left over, so most CTAs run two or
+    three segments of different units.  48 sampled rows against the oracle's
+    row-wise definition, and the whole block against the one-segment-per-CTA
+    schedule of the same variant (the same operations per node in the same
+    order, so the two agree to rounding)."""
+    import paper_2510_10529_b300 as P
+    wl = W.cube32_q4_hx()
+    mesh = fe.Mesh(wl.lo, wl.hi, wl.ncell, wl.order)
+    pb = P.Problem(wl.lo, wl.hi, wl.ncell, wl.order, nstates=8)
+    v = W.smeared_coulomb(pb.coords(), wl.nuclei_R, wl.nuclei_Z, wl.smear)
+    pb.set_potential(_cuda(v))
+    X = _cuda(W.random_block(mesh.L, 64, wl.seed), dtype)
+    rng = np.random.default_rng(11)
+    rows = np.concatenate([rng.integers(0, mesh.L, 44), [0, mesh.L - 1, mesh.Ni - 1, mesh.L // 2]])
+    Xd = X.double()
+
+    def fetch(idx):
+        return Xd[torch.as_tensor(idx, device="cuda")].cpu().numpy()
+
+    Yo = fe.htilde_rows(mesh, v[rows], rows, fetch)
+    n32, n64 = pb.tune_hx(-1, 0)
+    for variant in range(n64 if dtype == torch.float64 else n32):
+        pb.tune_hx(variant, wl.ncell)
+        Yw = pb.apply_h(X, tensor_cores=False)
+        pb.tune_hx(variant, BALANCED)
+        Yb = pb.apply_h(X, tensor_cores=False)
+        Yg = Yb[torch.as_tensor(rows, device="cuda")].double().cpu().numpy()
+        err = float((np.linalg.norm(Yg - Yo, axis=1) / np.linalg.norm(Yo, axis=1)).max())
+        diff = float((Yb.double() - Yw.double()).abs().max() / Yw.double().abs().max())
+        print(f"balanced schedule {dtype} variant {variant}: sampled rows {err:.2e}, "
+              f"vs whole-z schedule {diff:.1e}")
+        assert err <= tol
+        assert diff <= tol
