@@ -67,7 +67,7 @@ METRIC = "inverse-DFT iterations/s (mixed FP32/TF32 + FP64 GPU path)"
 # dram__bytes_write.sum of hx_sweep_kernel on the 24^3-cell Q4 mesh (857,375
 # unknowns) with 60 columns, tile variant 2, z segments of 6 cells
 # (profiles/hx_sweep_cube24_q4_60cols.md): 245,347,328 + 170,093,312 bytes.
-HX_SWEEP_DRAM_BYTES_PER_NODE_COL = (245347328 + 170093312) / (857375 * 60)
+HX_SWEEP_DRAM_BYTES_PER_NODE_COL = (245464832 + 169656832) / (857375 * 60)
 HX_SWEEP_DRAM_SOURCE = "profiles/hx_sweep_cube24_q4_60cols.md"
 
 def parse():
