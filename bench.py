@@ -521,6 +521,7 @@ def run_ours(args, rank, world):
         torch.cuda.profiler.stop()
     launches = P.invdft_kernel_launches() - launches0
     prof = pb.profile_hx(False)
+    defl = pb.profile_deflation()
     clk = clocks.stop()
     ms = dev_ms / args.steps
     ms_max = max_over_ranks(ms, world, device)
@@ -577,6 +578,20 @@ def run_ours(args, rank, world):
                 "columns_per_launch": km["columns_per_launch"],
                 "peak_source": "measured" if pk else "fallback",
                 "algorithmic_bytes_per_launch": km["algorithmic_bytes_per_launch"]}
+    def defl_summary(k, label):
+        r = defl[k]
+        nl = int(r["launches"])
+        if nl == 0:
+            return None
+        ach = r["bytes"] / (r["ms"] * 1e6)
+        return {"kernel": label, "launches": nl, "avg_launch_ms": r["ms"] / nl,
+                "algorithmic_bytes_per_launch": r["bytes"] / nl, "achieved_gbs": ach,
+                "hbm_frac": ach / peak_gbs, "ms_per_step": r["ms"] / args.steps}
+
+    deflation = {"gram": defl_summary("gram", "defl_gram_tc_kernel: C = Psi^T Z of the MINRES "
+                                      "deflation (tcgen05, split TF32)"),
+                 "update": defl_summary("update", "defl_update_tc_kernel: Z -= Psi C with the "
+                                        "fused column dot (tcgen05, split TF32)")}
     col_applies = sum(prof[k]["flops"] for k in prof) / (2.0 * ne * ne * cells)
     rates = measured_rates()
     hx = None if args.no_hx else hx_benchmark(device, rates=rates)
@@ -605,6 +620,7 @@ def run_ours(args, rank, world):
         "clocks": clk, "hx": hx, "fp64_gpu": fp64, "small_workload_gpu": small,
         "measured_rates_tflops": rates,
         "hx_in_step": {"minres": km, "filter": kf, "filter_tf32": kt},
+        "deflation_in_step": deflation,
         "step_stats": {"loss_last": stats[-1]["loss"], "err_l2_last": stats[-1]["err_l2"],
                        "err_l2": traj,
                        "cheb_passes": [s["cheb_passes"] for s in stats],

@@ -275,6 +275,15 @@ invdft_status invdft_batch_set_wait_limit(invdft_batch batch, int polls);
  * invdft_graph_stats: out3 = {graphs captured, graph replays, captures the
  * runtime refused (the work then ran as plain launches)}, process-wide.     */
 invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16);
+/* invdft_profile_deflation: while the timing of invdft_profile_hx is on, the
+ * tensor-core deflation launches of the FP32 MINRES iterations (blocks of 16
+ * or more columns) are timed the same way.  Drains pending events and writes
+ * the totals since the last enable: out8[0..3] = Gram C = Psi^T Z {device ms,
+ * algorithmic bytes ((n_psi + n_z) x 4 per node: Psi and Z read once), 0,
+ * launches}, out8[4..7] = update Z -= Psi C {ms, bytes ((n_psi + 3 n_z) x 4
+ * per node with the fused column dot: Psi, Z and V read, Z written), 0,
+ * launches}.  EINVAL for a NULL handle or out8, ECUDA on a CUDA error.       */
+invdft_status invdft_profile_deflation(invdft_handle h, double *out8);
 
 /* Tuning of H~X (no counterpart in the paper).  On orders 2 and 4, FP32 and
  * FP64 blocks whose rows are a multiple of 16 bytes run in the sweep form: a

@@ -155,6 +155,16 @@ def invdft_profile_hx(h, enable: bool):
             "fp32": dict(zip(keys, out[8:12])), "tf32": dict(zip(keys, out[12:]))}
 
 
+def invdft_profile_deflation(h):
+    """Totals of the tensor-core deflation launches (Gram, update) timed while
+    invdft_profile_hx is enabled."""
+    out = np.zeros(8)
+    _ok("invdft_profile_deflation",
+        lib.invdft_profile_deflation(h, out.ctypes.data_as(C.c_void_p)), h, False)
+    keys = ("ms", "bytes", "flops", "launches")
+    return {"gram": dict(zip(keys, out[:4])), "update": dict(zip(keys, out[4:]))}
+
+
 def invdft_tune_hx(h, variant: int = -1, seglen: int = 0):
     """Fix the tile variant (-1: autotuned) and z-segment length (0: autotuned)
     of the sweep H~X; returns the number of FP32 and FP64 variants."""
@@ -348,6 +358,9 @@ class Problem:
 
     def profile_hx(self, enable: bool):
         return invdft_profile_hx(self.h, enable)
+
+    def profile_deflation(self):
+        return invdft_profile_deflation(self.h)
 
     def tune_hx(self, variant: int = -1, seglen: int = 0):
         return invdft_tune_hx(self.h, variant, seglen)

@@ -108,6 +108,7 @@ def _load():
         "invdft_apply_h_dense": [H, P, P, P, C.c_int, C.c_int, P],
         "invdft_grad_to_q1": [H, C.c_int, P, P, P],
         "invdft_profile_hx": [H, C.c_int, P],
+        "invdft_profile_deflation": [H, P],
         "invdft_tune_hx": [H, C.c_int, C.c_int, P],
         "invdft_hx_config": [H, C.c_int, C.c_int, P],
         "invdft_kernel_launches": [C.POINTER(C.c_ulonglong)],

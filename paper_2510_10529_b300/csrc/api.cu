@@ -492,12 +492,25 @@ invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16) {
     }
   }
   if (enable) {
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < kProfKinds; ++t) {
       p.ms[t] = p.bytes_sum[t] = p.flops_sum[t] = 0.0;
       p.n[t] = 0;
     }
   }
   p.on = enable != 0;
+  return INVDFT_OK;
+}
+
+invdft_status invdft_profile_deflation(invdft_handle h, double *out8) {
+  if (!h || !out8) return INVDFT_EINVAL;
+  HxProf &p = h->prof;
+  if (!cuda_ok(h, prof_flush(h), "profile flush")) return INVDFT_ECUDA;
+  for (int t = 0; t < 2; ++t) {
+    out8[4 * t + 0] = p.ms[4 + t];
+    out8[4 * t + 1] = p.bytes_sum[4 + t];
+    out8[4 * t + 2] = 0.0;
+    out8[4 * t + 3] = (double)p.n[4 + t];
+  }
   return INVDFT_OK;
 }
 

@@ -392,22 +392,6 @@ template <typename T>
 cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   HxProf &p = c->prof;
   if (!p.on) return dispatch_hx(c, a, s);
-  const int slots = 1024;
-  if (p.ev.empty()) {
-    p.ev.resize(2 * slots);
-    p.kind.resize(slots);
-    p.bytes.resize(slots);
-    p.flops.resize(slots);
-    for (auto &e : p.ev) {
-      cudaError_t r = cudaEventCreate(&e);
-      if (r != cudaSuccess) return r;
-    }
-  }
-  if (p.used == slots) {
-    cudaError_t r = prof_flush(c);
-    if (r != cudaSuccess) return r;
-  }
-  const int k = p.used++;
   const double L = (double)c->L, n = a.ncol, sz = sizeof(T);
   // kinds: 0 FP64, 1 FP32 with the filter's W / E terms, 2 other FP32 (the
   // MINRES operator), 3 TF32 tensor cores
@@ -419,16 +403,41 @@ cudaError_t hx_op_t(Ctx *c, const HxArgs<T> &a, cudaStream_t s) {
   if (a.E) bytes += n * 4.0 * L;
   const double ne = (double)c->g.q * c->g.q * c->g.q;
   const double cells = (double)c->g.nc[0] * c->g.nc[1] * c->g.nc[2];
-  p.kind[k] = kind;
-  p.bytes[k] = bytes;
-  p.flops[k] = 2.0 * ne * ne * n * cells;
-  cudaEventRecord(p.ev[2 * k], s);
+  const int k = prof_begin(c, kind, bytes, 2.0 * ne * ne * n * cells, s);
   cudaError_t r = dispatch_hx(c, a, s);
-  cudaEventRecord(p.ev[2 * k + 1], s);
+  prof_end(c, k, s);
   return r;
 }
 
 }  // namespace
+
+int prof_begin(Ctx *c, int kind, double bytes, double flops, cudaStream_t s) {
+  HxProf &p = c->prof;
+  if (!p.on) return -1;
+  const int slots = 1024;
+  if (p.ev.empty()) {
+    p.ev.resize(2 * slots);
+    p.kind.resize(slots);
+    p.bytes.resize(slots);
+    p.flops.resize(slots);
+    for (auto &e : p.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        p.on = false;      // no timing rather than a failed launch
+        return -1;
+      }
+  }
+  if (p.used == slots && prof_flush(c) != cudaSuccess) return -1;
+  const int k = p.used++;
+  p.kind[k] = kind;
+  p.bytes[k] = bytes;
+  p.flops[k] = flops;
+  cudaEventRecord(p.ev[2 * k], s);
+  return k;
+}
+
+void prof_end(Ctx *c, int slot, cudaStream_t s) {
+  if (slot >= 0) cudaEventRecord(c->prof.ev[2 * slot + 1], s);
+}
 
 cudaError_t prof_flush(Ctx *c) {
   HxProf &p = c->prof;

@@ -92,19 +92,28 @@ struct Arena {
   }
 };
 
-// CUDA-event timing of every H~X launch while enabled (benchmark evidence):
-// per precision (0 = FP64, 1 = FP32) the summed device time, algorithmic
-// bytes, nominal dense-cell flops and launch count.
+// CUDA-event timing of every H~X launch, and of the tensor-core deflation
+// launches of the MINRES iterations, while enabled (benchmark evidence): per
+// kind the summed device time, algorithmic bytes, nominal dense-cell flops
+// (H~X) and launch count.
+constexpr int kProfKinds = 6;
 struct HxProf {
   bool on = false;
   std::vector<cudaEvent_t> ev;     // 2 per slot
   std::vector<int> kind;
   std::vector<double> bytes, flops;
   int used = 0;
-  // kinds: 0 FP64, 1 FP32 with W / E terms (filter), 2 other FP32, 3 TF32
-  double ms[4] = {0, 0, 0, 0}, bytes_sum[4] = {0, 0, 0, 0}, flops_sum[4] = {0, 0, 0, 0};
-  long long n[4] = {0, 0, 0, 0};
+  // kinds: 0 FP64, 1 FP32 with W / E terms (filter), 2 other FP32, 3 TF32;
+  // 4 deflation Gram, 5 deflation update (tcgen05, FP32 blocks)
+  double ms[kProfKinds] = {}, bytes_sum[kProfKinds] = {}, flops_sum[kProfKinds] = {};
+  long long n[kProfKinds] = {};
 };
+// Bracket one launch of the given kind with CUDA events on stream s (a no-op
+// returning -1 while timing is off); prof_end closes the slot prof_begin
+// returned.
+struct Ctx;
+int prof_begin(Ctx *c, int kind, double bytes, double flops, cudaStream_t s);
+void prof_end(Ctx *c, int slot, cudaStream_t s);
 
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) that only ever raises a
 // kernel's limit (api.cu).  Several host threads may launch the same kernel

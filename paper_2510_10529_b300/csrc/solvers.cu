@@ -511,12 +511,19 @@ invdft_status deflate(Ctx *c, const T *Psi, int nv, T *Z, int no, cudaStream_t s
   // padded FP32 blocks (Psi width a multiple of 8, Z width of 4)
   if (no >= 16) {
     // Gram and update on the tensor cores (tcgen05, operands split into two
-    // TF32 terms), the column dot fused into the update
+    // TF32 terms), the column dot fused into the update; timed while the
+    // handle's launch timing is on (algorithmic bytes: Psi and Z read for the
+    // Gram; Psi, Z and V read and Z written for the update)
+    const double L = (double)c->L;
+    int k = prof_begin(c, 4, (nv + no) * 4.0 * L, 0.0, s);
     CU(launch_defl_gram_tc((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial,
                            c->status + kStWaitGram, c->nsm, s), "gram(deflate)");
+    prof_end(c, k, s);
+    k = prof_begin(c, 5, (nv + (V ? 3 : 2) * no) * 4.0 * L, 0.0, s);
     CU(launch_defl_update_tc((const float *)Psi, nv, Cp, no, c->L, (float *)Z, -1.0,
                              (const float *)V, dot, c->partial, c->status + kStWaitUpdate,
                              c->nsm, s), "update(deflate)");
+    prof_end(c, k, s);
   } else {
     // narrow blocks: one row per thread keeps every thread busy
     CU(launch_defl_gram_f32((const float *)Psi, nv, (const float *)Z, no, c->L, Cp, c->partial, s),

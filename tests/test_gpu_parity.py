@@ -339,3 +339,27 @@ def test_bench_shape_forward_and_adjoint_match_oracle(bench_shape, prec):
     assert drho <= 1e-6
     assert abs(loss - L_ora) <= 1e-8 * L_ora
     assert gerr <= 1e-5
+
+
+def test_profile_deflation_counts_tensor_core_launches(bench_shape):
+    """With launch timing on, the tensor-core deflation Gram and update of the
+    FP32 MINRES block (about 50 columns here) are timed launch by launch: as
+    many updates as Grams, each with the stated algorithmic bytes per node."""
+    wl, mesh, v_fixed, rho_d, v_xc, _ = bench_shape
+    pb = _problem(-8.0, 8.0, 6, 4, nstates=wl.nstates, n_electrons=wl.n_electrons, kT=wl.kT,
+                  prec="mixed", eig_tol=1e-10, adj_tol=1e-11, cheb_degree=wl.cheb_degree)
+    pb.set_potential(_cuda(v_fixed), _cuda(v_xc))
+    pb.profile_hx(True)
+    pb.loss_grad(_cuda(rho_d), _cuda(np.ones(mesh.L)))
+    pb.profile_hx(False)
+    d = pb.profile_deflation()
+    ng, nu = int(d["gram"]["launches"]), int(d["update"]["launches"])
+    print(f"deflation launches: gram {ng} ({d['gram']['ms']:.2f} ms), "
+          f"update {nu} ({d['update']['ms']:.2f} ms)")
+    assert ng > 0 and ng == nu
+    assert d["gram"]["ms"] > 0 and d["update"]["ms"] > 0
+    # Gram: (n_psi + n_z) columns of 4 bytes per node; update: n_psi + 2 or 3 n_z
+    per_node_g = d["gram"]["bytes"] / ng / (4.0 * pb.L)
+    per_node_u = d["update"]["bytes"] / nu / (4.0 * pb.L)
+    assert abs(per_node_g - round(per_node_g)) < 1e-9 and 2 * 50 <= per_node_g <= 2 * 64 + 8
+    assert per_node_u > per_node_g
