@@ -203,11 +203,12 @@ def measured_rates():
         return {"error": repr(exc)}
 
 
-def hx_benchmark(device, reps32=20, reps64=3, rates=None):
+def hx_benchmark(device, reps32=50, reps64=50, rates=None):
     """H~X on the 32^3-cell Q4 operator benchmark (64 unit-norm random vectors):
     TF32 tensor cores (dense cell GEMM), FP32 and FP64 sweep form (CUDA cores).
-    Each timing is the mean over `reps` back-to-back launches after warm-up;
-    the blocks (0.5 GB FP32, 1.05 GB FP64) are larger than L2."""
+    Each timing is the median over `reps` launches, each between its own pair
+    of CUDA events, after 5 warm-up launches (the autotuner's first launch
+    among them); the blocks (0.5 GB FP32, 1.05 GB FP64) are larger than L2."""
     import torch
 
     import paper_2510_10529_b300 as P
@@ -225,17 +226,17 @@ def hx_benchmark(device, reps32=20, reps64=3, rates=None):
     for name, X, reps, tc in (("tf32", X64.float(), reps32, True),
                               ("fp32", X64.float(), reps32, False), ("fp64", X64, reps64, False)):
         Y = torch.empty_like(X)
-        for _ in range(3):
+        for _ in range(5):
             P.invdft_apply_h(pb.h, X, Y, tc)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for e0, e1 in ev:
+            e0.record()
             P.invdft_apply_h(pb.h, X, Y, tc)
-        e1.record()
+            e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in ev)
         # X read, Y written, v read (FP32 copy on the FP32 CUDA-core path)
         vbytes = 4 if name == "fp32" else 8
         byt = (2 * 64 * X.element_size() + vbytes) * pb.L
