@@ -285,18 +285,19 @@ invdft_status invdft_profile_hx(invdft_handle h, int enable, double *out16);
  * launches}.  EINVAL for a NULL handle or out8, ECUDA on a CUDA error.       */
 invdft_status invdft_profile_deflation(invdft_handle h, double *out8);
 
-/* Tuning of H~X (no counterpart in the paper).  On orders 2 and 4, FP32 and
- * FP64 blocks whose rows are a multiple of 16 bytes run in the sweep form: a
+/* Tuning of H~X (no counterpart in the paper).  On orders 2, 4 and 6, FP32
+ * and FP64 blocks whose rows are a multiple of 16 bytes run in the sweep form: a
  * CTA owns a column of nodes of the x-y plane and a chunk of columns, and
  * walks a segment of the z range.  Several tile variants exist (columns per
  * CTA, tile height, planes in flight, x-cells per task).
  * invdft_tune_hx: variant >= 0 fixes the tile variant, seglen > 0 the segment
  * length (in cells) for every later H~X launch of this handle; -1 / 0 leave
  * them to the autotuner, which on the first launch of each (precision, ncol,
- * epilogue) that is not being captured into a graph times every variant with
- * the whole z range, halves, quarters, segments short enough for two CTAs
- * per SM and the balanced schedule, and keeps the fastest (launches inside a
- * capture before that take variant 0 with the short segments).
+ * epilogue) on a mesh of 2^18 unknowns or more that is not being captured
+ * into a graph times every variant with the whole z range, halves, quarters,
+ * segments short enough for two CTAs per SM and the balanced schedule, and
+ * keeps the fastest (smaller meshes, and launches inside a capture before
+ * that, take variant 0 with the short segments).
  * seglen = INVDFT_HX_SEG_BALANCED fixes the balanced schedule: a persistent
  * grid of one CTA per resident slot that takes whole (tile, column chunk)
  * units round-robin and then an equal share of the z-cells of the units left
