@@ -143,3 +143,31 @@ def test_device_calls_validate_on_the_host_first():
         assert lib.invdft_batch_create(None, 1, C.byref(out)) == INVDFT_EINVAL
     finally:
         P.invdft_destroy(h)
+
+
+def test_tuning_and_timing_calls_on_the_host():
+    """The tuning and timing entry points work on a handle without a GPU: the
+    balanced H~X schedule is accepted as a fixed segment length, negative
+    lengths and variants out of range are rejected, nothing is tuned before
+    the first launch, and the deflation timing totals start at zero."""
+    import numpy as np
+
+    import paper_2510_10529_b300 as P
+    from paper_2510_10529_b300._lib import INVDFT_EINVAL, INVDFT_OK, lib
+    h, _ = P.invdft_create_mesh(P.MeshDesc.make(-4.0, 4.0, 2, 4),
+                                P.Opts(nstates=2, n_electrons=2.0))
+    try:
+        n32, n64 = P.invdft_tune_hx(h, 0, P.INVDFT_HX_SEG_BALANCED)
+        assert n32 >= 1 and n64 >= 1
+        assert lib.invdft_tune_hx(h, 0, -5, None) == INVDFT_EINVAL
+        assert lib.invdft_tune_hx(h, max(n32, n64), 0, None) == INVDFT_EINVAL
+        assert lib.invdft_tune_hx(h, -1, 0, None) == INVDFT_OK
+        cfg = P.invdft_hx_config(h, 60, False)
+        assert all(v == (-1, -1) for v in cfg.values())
+        d = P.invdft_profile_deflation(h)
+        assert all(d[k][f] == 0.0 for k in ("gram", "update") for f in ("ms", "bytes", "launches"))
+        assert lib.invdft_profile_deflation(h, None) == INVDFT_EINVAL
+        assert lib.invdft_profile_deflation(None, np.zeros(8).ctypes.data_as(C.c_void_p)) \
+            == INVDFT_EINVAL
+    finally:
+        P.invdft_destroy(h)
